@@ -1,0 +1,100 @@
+"""Pins of the alignment objective and its gradient (the differentiation
+workload: the least-squares fit of the tracklet filter applied to every
+track, summed, as a function of per-module placement parameters)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_03936_gb300 import synth
+
+SIGMA = 0.012
+
+
+def truth_tracks(ev):
+    """Particles with >= 3 hits as fixed tracks, hits in traversal order."""
+    mc = ev.mc
+    idx = np.nonzero(mc >= 0)[0]
+    order = np.lexsort((ev.module[idx], mc[idx]))
+    idx = idx[order]
+    pid = mc[idx]
+    starts = np.concatenate([[0], np.nonzero(np.diff(pid))[0] + 1, [len(idx)]])
+    lens = np.diff(starts)
+    keep = np.repeat(lens >= 3, lens)
+    idx = idx[keep]
+    lens = lens[lens >= 3]
+    ho = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    return ho, idx.astype(np.int32)
+
+
+@pytest.fixture(scope="module")
+def aligned_events():
+    ev = synth.make_events(5, 12, workers=1)
+    ho, th = truth_tracks(ev)
+    return ev, ho, th
+
+
+def f(ev, ho, th, align):
+    return oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, align, SIGMA,
+                             want_grad=False)[0]
+
+
+def test_gradient_matches_central_differences(aligned_events):
+    ev, ho, th = aligned_events
+    rng = np.random.default_rng(4)
+    align = np.concatenate([rng.normal(0, 0.005, (52, 3)), rng.normal(0, 5e-5, (52, 3))], 1)
+    v, g = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, align, SIGMA)
+    assert abs(v - f(ev, ho, th, align)) == 0.0
+    fd = np.zeros_like(g)
+    for m in range(52):
+        for k in range(6):
+            h = 1e-4 if k < 3 else 1e-5
+            ap = align.copy(); ap[m, k] += h
+            am = align.copy(); am[m, k] -= h
+            fd[m, k] = (f(ev, ho, th, ap) - f(ev, ho, th, am)) / (2 * h)
+    scale = np.abs(fd).max()
+    err = np.abs(g - fd)
+    assert (err <= 1e-6 * np.maximum(np.abs(fd), 1e-3 * scale)).all(), err.max()
+
+
+def test_global_motions_leave_chi2_unchanged(aligned_events):
+    # translating every module, or rotating every module about the beam (z)
+    # axis, moves all hits rigidly: every line refits to the same chi2
+    ev, ho, th = aligned_events
+    rng = np.random.default_rng(5)
+    align = np.concatenate([rng.normal(0, 0.005, (52, 3)), rng.normal(0, 5e-5, (52, 3))], 1)
+    _, g = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, align, SIGMA)
+    # at align != 0 only the translations are rigid motions of the aligned hits
+    tot = np.abs(g).sum(0)
+    for k in (0, 1, 2):
+        assert abs(g[:, k].sum()) <= 1e-9 * tot[k]
+    _, g0 = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z,
+                              np.zeros((52, 6)), SIGMA)
+    tot0 = np.abs(g0).sum(0)
+    for k in (0, 1, 2, 5):
+        assert abs(g0[:, k].sum()) <= 1e-9 * tot0[k]
+
+
+def test_exact_lines_have_zero_chi2_and_gradient():
+    from tests.hand_events import line_hits, assemble
+    parts = [line_hits(5.0 + i, -3.0 + 0.5 * i, 0.002 * i, -0.001, range(4 + i, 30 + i))
+             for i in range(5)]
+    x, y, z, m, g = assemble(parts)
+    ho = np.concatenate([[0], np.cumsum([len(p) for p in g])]).astype(np.int32)
+    th = np.concatenate(g).astype(np.int32)
+    mz = synth.module_z_traversal()
+    v, gr = oracle.align_chi2(x, y, z, m, ho, th, mz, np.zeros((52, 6)), SIGMA)
+    # only fp32 representation of the hits remains (~1e-6 mm per coordinate)
+    assert v < 1e-3
+    assert np.abs(gr).max() < 1.0
+
+
+def test_objective_at_zero_equals_sum_of_track_fits(aligned_events):
+    ev, ho, th = aligned_events
+    v, _ = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z,
+                             np.zeros((52, 6)), SIGMA, want_grad=False)
+    tot = 0.0
+    for t in range(len(ho) - 1):
+        h = th[ho[t]:ho[t + 1]]
+        _, c2 = oracle.fit(ev.x[h], ev.y[h], ev.z[h], SIGMA)
+        tot += float(c2)
+    assert abs(v - tot) <= 1e-3 * v
