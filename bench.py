@@ -1,0 +1,331 @@
+"""Throughput benchmark of the GB300 Search-by-triplet library.
+
+A step reconstructs one batch of synthetic events (100k uneven events, pileup
+U(1, 20), 200-12600 hits each; inputs larger than L2) through the batched C
+entry point (persistent work-queue kernel replayed from a CUDA graph).  The
+line also reports the plain one-block-per-event launch on the same batch,
+the end-to-end host entry point (copies inside the timed region), the
+alignment adjoint, the dominant kernel's roofline fraction, the SM clocks
+seen during the timed region and the CPU oracle timed on host cores over a
+bounded sample, whose tracks are compared with the GPU's event by event.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank reconstructs its own batch (independent events, no
+collective on the data path) and rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VELO events/s on 1 GB300, batched vs plain; p99 latency; track-set match"
+WORKLOAD = "uneven batch: 100k events, pileup U(1,20), Poisson(25)+10% backward tracks per vertex"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--events", type=int, default=100_000)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read-only)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(ev, budget_s: float, gpu_out=None):
+    """The oracle on all host cores over a bounded sample of the workload's
+    events; optionally compares its tracks with the GPU's for those events."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1)
+    order = rng.permutation(ev.n_events)
+    done, t_total, n_match, n_cmp = 0, 0.0, 0, 0
+    chunk = 500
+    while done < ev.n_events and t_total < budget_s:
+        idx = np.sort(order[done:done + chunk])
+        sub_off = [0]
+        xs, ys, zs, ms = [], [], [], []
+        for e in idx:
+            lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+            xs.append(ev.x[lo:hi]); ys.append(ev.y[lo:hi]); zs.append(ev.z[lo:hi]); ms.append(ev.module[lo:hi])
+            sub_off.append(sub_off[-1] + hi - lo)
+        x, y, z, m = (np.concatenate(a) for a in (xs, ys, zs, ms))
+        sub_off = np.array(sub_off, np.int32)
+        t0 = time.perf_counter()
+        r = oracle.reconstruct(x, y, z, m, sub_off, ev.module_z, n_threads=cores)
+        t_total += time.perf_counter() - t0
+        if gpu_out is not None:
+            to, ho, th, prm = (gpu_out["track_offsets"], gpu_out["hit_offsets"], gpu_out["track_hits"],
+                               gpu_out["params"])
+            for j, e in enumerate(idx):
+                g0, g1 = to[e], to[e + 1]
+                o0, o1 = r.track_offsets[j], r.track_offsets[j + 1]
+                gh = th[ho[g0]:ho[g1]] - ev.event_offsets[e]
+                oh = r.track_hits[r.hit_offsets[o0]:r.hit_offsets[o1]] - sub_off[j]
+                same = (g1 - g0 == o1 - o0 and np.array_equal(gh, oh)
+                        and np.array_equal(prm[g0:g1].view(np.uint32), r.params[o0:o1].view(np.uint32)))
+                n_match += int(same)
+                n_cmp += 1
+        done += len(idx)
+    res = {"value": done / t_total, "unit": "events/s", "cores": cores, "kind": "oracle",
+           "sample": f"{done} events drawn at random from the workload, {t_total:.1f} s wall on {cores} threads"}
+    match = {"events_compared": n_cmp, "bit_exact_events": n_match} if gpu_out is not None else None
+    return res, match
+
+
+def run_reference(args, ws, rank):
+    from paper_2207_03936_gb300 import synth
+    if rank != 0:
+        return
+    ev = synth.make_events(3, args.events)
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res, _ = cpu_baseline(ev, args.cpu_seconds / max(args.steps, 1))
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            per_step.append(res["value"])
+    v = float(np.mean(per_step))
+    res["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events": ev.n_events, "hits": ev.n_hits},
+            "cpu_baseline": res,
+            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    from paper_2207_03936_gb300 import synth
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    # inputs are drawn before any CUDA call (the generator uses spawned workers)
+    ev = synth.make_events(3, args.events, seed=rank)
+    ev_adj = None if args.no_adjoint else synth.make_events(5)
+
+    import torch
+    from paper_2207_03936_gb300 import sbt
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    dev = [torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+    # per-event capacity sized to the batch (shared memory per block scales with it)
+    nmax = int(-(-int(np.diff(ev.event_offsets).max()) // 1024) * 1024)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(max_hits_per_event=nmax))
+    threads = sbt.sbt_autotune(h, *dev)
+    out = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sbt.sbt_reconstruct_batched(h, *dev, out=out)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        sbt.sbt_reconstruct_batched(h, *dev, out=out)
+        launches += h.last_launch_count()
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    ms_max = ms
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_max = float(t.item())
+    total_events = ev.n_events * ws
+    value = total_events / (ms_max / 1e3)
+    gpu_res = out.compact()
+    counts = gpu_res["counts"]
+
+    # per-kernel times (no graph, CUDA events on the launching stream)
+    kms = sbt.sbt_profile_batched(h, *dev, out, reps=3)
+    T, H = int(counts[0]), int(counts[1])
+    # algorithmic bytes of the persistent kernel: hits in (x, y, z, module: 16 B),
+    # event offsets, staged hit indices and track lengths out, per-event counts
+    alg_bytes = 16 * ev.n_hits + 4 * (ev.n_events + 1) + 4 * H + T + 12 * ev.n_events
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (kms[1] / 1e3) / 1e9
+
+    plain = None
+    if not args.no_plain:
+        pout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
+        sbt.sbt_reconstruct(h, *dev, out=pout)
+        torch.cuda.synchronize()
+        a.record(stream)
+        n_plain = max(1, min(args.steps, 3))
+        for _ in range(n_plain):
+            sbt.sbt_reconstruct(h, *dev, out=pout)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / n_plain
+        same = all(np.array_equal(v, pout.compact()[k]) for k, v in gpu_res.items())
+        plain = {"value": ev.n_events / (pms / 1e3), "unit": "events/s", "ms_per_step": pms,
+                 "identical_to_batched": bool(same)}
+        del pout
+
+    # end to end through the host entry point (pinned host buffers)
+    host_in = [torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+    hout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, pin_memory=True)
+    sbt.sbt_reconstruct_host(h, *host_in, out=hout)
+    n_e2e = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sbt.sbt_reconstruct_host(h, *host_in, out=hout)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    h2d = 16 * ev.n_hits + 4 * (ev.n_events + 1)
+    d2h = 16 + 4 * (ev.n_events + 1) + 4 * ev.n_events + 4 * (T + 1) + 4 * H + 24 * T
+    e2e = {"value": ev.n_events / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+    del hout, host_in
+
+    adj = None
+    if ev_adj is not None:
+        ad = [torch.from_numpy(a).cuda() for a in (ev_adj.x, ev_adj.y, ev_adj.z, ev_adj.module,
+                                                     ev_adj.event_offsets)]
+        r = sbt.sbt_reconstruct_batched(h, *ad)
+        rc = r.compact()
+        ho = torch.from_numpy(rc["hit_offsets"]).cuda()
+        th = torch.from_numpy(rc["track_hits"]).cuda()
+        align = torch.zeros(52, 6, dtype=torch.float64, device="cuda")
+        sbt.sbt_fit_adjoint(h, ad[0], ad[1], ad[2], ad[3], ho, th, align)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            sbt.sbt_fit_adjoint(h, ad[0], ad[1], ad[2], ad[3], ho, th, align)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ams = a.elapsed_time(b) / args.steps
+        adj = {"value": ev_adj.n_events / (ams / 1e3), "unit": "events/s", "ms_per_step": ams,
+               "events": ev_adj.n_events, "tracks": int(rc["counts"][0]), "dtype": "f64"}
+    h.close()
+
+    if rank == 0:
+        cpu, match = cpu_baseline(ev, args.cpu_seconds, gpu_res)
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events": ev.n_events, "hits": ev.n_hits,
+                       "hits_per_event_max": int(np.diff(ev.event_offsets).max()),
+                       "tracks": T, "threads_per_block": threads,
+                       "l2": "inputs larger than L2 (no flush needed)"},
+            "plain": plain,
+            "match": match,
+            "adjoint": adj,
+            "e2e": e2e,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_reco_persistent", "kernel_ms": kms[1],
+                         "kernel_ms_all": {"order": kms[0], "reco": kms[1], "scan": kms[2],
+                                           "consolidate": kms[3]}},
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

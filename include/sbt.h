@@ -1,0 +1,272 @@
+/*
+ * sbt.h — C ABI of the GB300 Search-by-triplet VELO track reconstruction.
+ *
+ * The method is the one of Cámpora Pérez, Neufeld and Riscos Núñez, "Search by
+ * triplet: An efficient local track reconstruction algorithm for parallel
+ * architectures" (arXiv 2207.03936), section "Search by triplet":
+ *   sort of each module's hits by phi, iterative triplet seeding and track
+ *   following with flagged hits, the tracklet filter, and consolidation of
+ *   the tracks (section "Results", sequence item "Data consolidation") with a
+ *   least-squares straight-line fit.
+ * The problem statement (section 1): find disjoint sets of hits compatible
+ * with straight trajectories; every hit belongs to at most one track.
+ *
+ * Conventions for every call:
+ *   - Pointers marked "device" must be CUDA device (or managed) memory of the
+ *     current device; "host" pointers are ordinary host memory.  The caller
+ *     owns all memory passed in; the library never frees it.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Compute entry points are asynchronous on that stream; only
+ *     argument validation is synchronous.
+ *   - Every call returns an sbt_status.  SBT_ERR_ARG: invalid arguments (no
+ *     work enqueued).  SBT_ERR_CUDA: a CUDA call failed (sbt_last_error has
+ *     the message).  Device-side per-event problems never fail the call: they
+ *     are reported in sbt_tracks.event_status and sbt_tracks.counts.
+ *   - A handle may be used from one host thread at a time, and its calls must
+ *     not overlap on the GPU (they share the handle's workspace): use one
+ *     handle per concurrent stream.
+ *   - Hit index types: the event-local hit count is at most 65533; batch hit
+ *     indices and offsets are int32.
+ */
+#ifndef SBT_H
+#define SBT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SBT_OK = 0,
+    SBT_ERR_ARG = 1,      /* invalid argument; nothing enqueued */
+    SBT_ERR_CAPACITY = 2, /* output or per-event capacity exceeded (device-reported) */
+    SBT_ERR_CUDA = 3,     /* CUDA runtime error; see sbt_last_error */
+    SBT_ERR_TIMEOUT = 4,  /* a bounded wait expired (serving) */
+    SBT_ERR_STATE = 5     /* call not valid in the object's current state */
+} sbt_status;
+
+typedef struct sbt_handle sbt_handle;
+
+/* Detector geometry (section 1, Fig. 2: planes of pixel modules along z).
+ * Module ids are given in traversal order: the reconstruction visits module
+ * 0, 1, 2, ... (section "Track seeding and track following": the direction of
+ * traversal is configurable, here by the order of module_z). */
+typedef struct {
+    int32_t n_modules;      /* 3 .. 64 */
+    const float* module_z;  /* host [n_modules]: plane z of module id i, mm; copied */
+    float r_min, r_max;     /* active annulus, mm (informational) */
+} sbt_geometry;
+
+/* Tunable constants.  The paper states that the thresholds are configurable
+ * but prints no values; the defaults below were fixed once on synthetic truth. */
+typedef struct {
+    int32_t k_doublets;          /* candidates per middle hit in seeding (Fig. 3: four); default 4 */
+    float max_scatter_seed;      /* seeding scatter cut dx^2+dy^2, mm^2; default 0.04 */
+    float max_scatter_follow;    /* following scatter cut, mm^2; default 0.04 */
+    float max_chi2_tracklet;     /* tracklet filter chi2 cut; default 20 */
+    float hit_sigma;             /* hit resolution for chi2, mm; default 0.012 */
+    int32_t max_hits_per_event;  /* events with more hits get SBT_ERR_CAPACITY; default 16384, <= 65533 */
+    int32_t max_forming_tracks;  /* per-event forming-track buffer; 0 = max(256, max_hits/16) */
+    int32_t threads_per_block;   /* 64, 128 or 256; 0 = 128 (batched: autotuned value if any) */
+} sbt_config;
+
+/* Reconstructed tracks, CSR over events and tracks.  All arrays are device
+ * memory allocated by the caller.  Sizing that can never overflow:
+ * cap_hits >= n_hits and cap_tracks >= n_hits / 3 (hits are disjoint and a
+ * track has at least 3 hits).
+ *   track_offsets [n_events + 1]   tracks of event e: [track_offsets[e], track_offsets[e+1])
+ *   hit_offsets   [cap_tracks + 1] hits of track t: track_hits[hit_offsets[t] .. hit_offsets[t+1])
+ *   track_hits    [cap_hits]       batch hit indices (into x/y/z), module (traversal) order
+ *   params        [cap_tracks * 4] x0, y0, tx, ty of x = x0 + tx z, y = y0 + ty z
+ *   chi2          [cap_tracks]     sum of squared residuals / hit_sigma^2
+ *   ndof          [cap_tracks]     2 * hits - 4
+ *   event_status  [n_events]       SBT_OK, SBT_ERR_ARG (module id out of range) or
+ *                                  SBT_ERR_CAPACITY (event above max_hits_per_event
+ *                                  or a per-event buffer full); failed events have no tracks
+ *   counts        [4]              required tracks, required track hits, SBT_OK or
+ *                                  SBT_ERR_CAPACITY when cap_* was too small (then
+ *                                  nothing beyond the capacities is written), number
+ *                                  of failed events
+ * Tracks of an event are ordered by their smallest hit index. */
+typedef struct {
+    int32_t* track_offsets;
+    int32_t* hit_offsets;
+    int32_t* track_hits;
+    float* params;
+    float* chi2;
+    int32_t* ndof;
+    int32_t* event_status;
+    int32_t* counts;
+    int32_t cap_tracks;
+    int32_t cap_hits;
+} sbt_tracks;
+
+/* Fills *out with the defaults. */
+sbt_status sbt_default_config(sbt_config* out);
+
+/* Creates a handle: copies the geometry and configuration (cfg NULL = defaults).
+ * Allocates only small device state; workspaces grow on first use. */
+sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_handle** out);
+
+/* Waits for the handle's pending work and frees everything it owns. */
+sbt_status sbt_destroy(sbt_handle* h);
+
+/* Message of the last failed call on this handle ("" if none); NULL handle
+ * gives the last creation error.  The string lives until the next call. */
+const char* sbt_last_error(const sbt_handle* h);
+
+/*
+ * Reconstruct a batch of events, one thread block per event (the paper's
+ * mapping of events to blocks and of hits and forming tracks to threads,
+ * Table 1).  Inputs (device): x, y, z [n_hits] fp32 mm, module [n_hits]
+ * traversal-order module id, event_offsets [n_events + 1] (event e owns hits
+ * [event_offsets[e], event_offsets[e+1])), n_hits = event_offsets[n_events].
+ * Outputs: *out (device arrays described at sbt_tracks).
+ */
+sbt_status sbt_reconstruct(sbt_handle* h, const float* x, const float* y, const float* z,
+                           const int32_t* module, const int32_t* event_offsets, int32_t n_events,
+                           int32_t n_hits, const sbt_tracks* out, void* stream);
+
+/*
+ * Same result as sbt_reconstruct, produced by one persistent launch whose
+ * blocks take events (largest first) from a device work queue; the launch
+ * sequence is captured once into a CUDA graph per distinct argument set and
+ * replayed.  Block size comes from sbt_autotune when it has run.
+ */
+sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y, const float* z,
+                                   const int32_t* module, const int32_t* event_offsets,
+                                   int32_t n_events, int32_t n_hits, const sbt_tracks* out,
+                                   void* stream);
+
+/*
+ * End-to-end form for callers holding host memory: copies the inputs (host)
+ * to the device, runs the batched reconstruction and copies the tracks back
+ * into host arrays of the sbt_tracks layout (out_host pointers are host
+ * memory; counts is host too).  Synchronous: returns when the host arrays are
+ * filled.  Pinned host memory gives full copy bandwidth.
+ */
+sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, const float* z,
+                                const int32_t* module, const int32_t* event_offsets,
+                                int32_t n_events, int32_t n_hits, const sbt_tracks* out_host,
+                                void* stream);
+
+/*
+ * Times the batched kernel for each block size in {64, 128, 256} on the given
+ * events (device inputs as in sbt_reconstruct) and keeps the fastest in the
+ * handle.  Results do not depend on the choice.  Synchronous.  *chosen
+ * (host, may be NULL) receives the block size.
+ */
+sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const float* z,
+                        const int32_t* module, const int32_t* event_offsets, int32_t n_events,
+                        int32_t n_hits, int32_t* chosen, void* stream);
+
+/*
+ * Differentiation of the consolidation fit with respect to per-module
+ * alignment.  For a hit h on module m with plane centre c = (0, 0, module_z[m])
+ * and align[6m .. 6m+5] = (dx, dy, dz, a, b, g) (mm, rad), the aligned hit is
+ *     h' = Rz(g) Ry(b) Rx(a) (h - c) + c + (dx, dy, dz).
+ * Every track (hit lists fixed, e.g. the output of sbt_reconstruct) is refitted
+ * by least squares on its aligned hits, in fp64; *chi2_sum = sum over tracks of
+ * the squared residuals / hit_sigma^2, grad = d chi2_sum / d align [n_modules*6],
+ * accumulated in fp64 in a fixed order (bitwise reproducible).
+ * Inputs (device): x, y, z, module [n_hits]; hit_offsets [n_tracks + 1];
+ * track_hits; align [n_modules * 6] fp64.  Outputs (device): chi2_sum [1],
+ * grad [n_modules * 6] fp64 (grad may be NULL for the value alone).
+ */
+sbt_status sbt_fit_adjoint(sbt_handle* h, const float* x, const float* y, const float* z,
+                           const int32_t* module, int32_t n_hits, const int32_t* hit_offsets,
+                           const int32_t* track_hits, int32_t n_tracks, const double* align,
+                           double* chi2_sum, double* grad, void* stream);
+
+/*
+ * Stage output of the phi sort (section "Sort by phi"), for checking it in
+ * isolation.  Outputs (device): phi16 [n_hits] in sorted order within each
+ * event, perm [n_hits] event-local input index of the hit at each sorted
+ * position, module_offsets [n_events * (n_modules + 1)] event-local.
+ */
+sbt_status sbt_debug_sort(sbt_handle* h, const float* x, const float* y, const int32_t* module,
+                          const int32_t* event_offsets, int32_t n_events, int32_t n_hits,
+                          uint16_t* phi16, int32_t* perm, int32_t* module_offsets, void* stream);
+
+/* phi16 of n points (device x, y in; device out): the mapping of [-pi, pi]
+ * onto the unsigned 16-bit range used by the sort (section "Sort by phi"). */
+sbt_status sbt_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out, void* stream);
+
+/*
+ * Measurement helper: runs the batched sequence `reps` times without a graph,
+ * timing each kernel with CUDA events on `stream`, and writes the mean
+ * milliseconds per launch to ms[4] (host): ordering kernel, persistent
+ * reconstruction kernel, scan, consolidation.  Synchronous.
+ */
+sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, const float* z,
+                               const int32_t* module, const int32_t* event_offsets,
+                               int32_t n_events, int32_t n_hits, const sbt_tracks* out, int32_t reps,
+                               float* ms, void* stream);
+
+/* Number of kernels the last reconstruction call on h enqueued (launch
+ * accounting for benchmarks); 0 before any call. */
+int32_t sbt_last_launch_count(const sbt_handle* h);
+
+/* ------------------------------------------------------------ serving --- */
+
+/*
+ * Continuous-batching request loop (no counterpart in the paper, which runs
+ * fixed bunches of events per stream; Results, "n events per bunch").  A
+ * background host thread admits submitted events into device slots while the
+ * device-memory budget allows, launches every admitted group at once on one
+ * of several streams (so newly admitted work overlaps work still running),
+ * copies results back and marks requests done.  Latency is measured from
+ * submission to completion on the host clock.
+ */
+typedef struct sbt_server sbt_server;
+
+/* Result of one request (host memory owned by the server until the request
+ * is released with sbt_server_release). */
+typedef struct {
+    int64_t request_id;
+    int32_t status;          /* event status (sbt_status) */
+    int32_t n_tracks;
+    const int32_t* hit_offsets;  /* [n_tracks + 1], hit indices are event-local */
+    const int32_t* track_hits;
+    const float* params;     /* [n_tracks * 4] */
+    const float* chi2;
+    double latency_s;        /* submit -> done */
+} sbt_result;
+
+/* memory_budget_bytes bounds the device memory of in-flight events (inputs,
+ * outputs, workspace); max_streams (1..16) bounds concurrent batches;
+ * max_batch_events bounds one launch. */
+sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t max_streams,
+                             int32_t max_batch_events, sbt_server** out);
+
+/* Copies one event (host arrays of n hits) into the server's queue. */
+sbt_status sbt_server_submit(sbt_server* s, int64_t request_id, const float* x, const float* y,
+                             const float* z, const int32_t* module, int32_t n);
+
+/* Up to max_results finished requests into results[] (host); *n_out receives
+ * the count.  Waits at most timeout_s for the first one (0 = do not wait);
+ * returns SBT_ERR_TIMEOUT when none finished in time. */
+sbt_status sbt_server_poll(sbt_server* s, sbt_result* results, int32_t max_results,
+                           int32_t* n_out, double timeout_s);
+
+/* Frees the host memory of a polled result. */
+sbt_status sbt_server_release(sbt_server* s, int64_t request_id);
+
+/* stats (host, 8 doubles): completed, submitted, batches launched, mean
+ * events per batch, peak device bytes in flight, failed batches, 0, 0. */
+sbt_status sbt_server_stats(sbt_server* s, double* stats);
+
+/* Makes the next launched batch fail on the host side (test hook for the
+ * failure path: the batch's requests complete with SBT_ERR_CUDA status and
+ * the loop continues). */
+sbt_status sbt_server_inject_failure(sbt_server* s);
+
+/* Stops the loop after finishing admitted work and frees the server. */
+sbt_status sbt_server_destroy(sbt_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBT_H */

@@ -1,0 +1,628 @@
+// C ABI of the library: handles, workspaces, launch sequences, the CUDA-graph
+// cache of the batched launch, the block-size autotuner and the end-to-end
+// host entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sbt_internal.h"
+
+using namespace sbt;
+
+namespace {
+
+std::string g_create_error;
+
+// One device allocation carved into aligned sub-arrays.
+struct Arena {
+    void* base = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t need)
+    {
+        if (need <= bytes) return cudaSuccess;
+        if (base) {
+            cudaError_t e = cudaFree(base);
+            base = nullptr;
+            bytes = 0;
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaMalloc(&base, need);
+        if (e != cudaSuccess) {
+            base = nullptr;
+            return e;
+        }
+        bytes = need;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (base) cudaFree(base);
+        base = nullptr;
+        bytes = 0;
+    }
+};
+
+struct Carver {
+    char* p;
+    size_t off = 0;
+    explicit Carver(void* base) : p((char*)base) {}
+    template <class T>
+    T* take(int64_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* r = (T*)(p ? p + off : nullptr);
+        off += sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+        return r;
+    }
+};
+
+// Scratch layout for `hits` hit slots over `regions` regions (see Work).
+size_t carve_work(void* base, int64_t hits, int64_t regions, Work* W)
+{
+    Carver c(base);
+    Work w;
+    w.coords = c.take<float4>(hits);
+    w.keys = c.take<uint32_t>(hits);
+    w.idxA = c.take<uint16_t>(hits);
+    w.idxB = c.take<uint16_t>(hits);
+    w.prev = c.take<uint16_t>(hits);
+    w.claim = c.take<unsigned long long>(hits);
+    w.tracklets = c.take<unsigned long long>(tracklet_entries(hits, regions));
+    w.tl_q = c.take<uint32_t>(tracklet_entries(hits, regions));
+    w.finals = c.take<uint32_t>(final_entries(hits, regions));
+    w.fin_rank = c.take<int32_t>(final_entries(hits, regions));
+    w.fin_start = c.take<int32_t>(final_entries(hits, regions));
+    if (W) *W = w;
+    return c.off + 256;
+}
+
+size_t carve_staging(void* base, int64_t n_hits, int64_t n_events, Staging* S)
+{
+    Carver c(base);
+    Staging s;
+    s.hits = c.take<int32_t>(n_hits);
+    s.len = c.take<uint8_t>(n_hits / 3 + n_events + 1);
+    s.ev_ntracks = c.take<int32_t>(n_events);
+    s.ev_nhits = c.take<int32_t>(n_events);
+    s.track_base = c.take<int32_t>(n_events);
+    s.hit_base = c.take<int32_t>(n_events);
+    s.order = c.take<int32_t>(n_events);
+    s.queue = c.take<int32_t>(4);
+    if (S) *S = s;
+    return c.off + 256;
+}
+
+struct GraphKey {
+    const void* ptrs[13];
+    int64_t vals[6];
+    bool operator==(const GraphKey& o) const
+    {
+        return std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && std::memcmp(vals, o.vals, sizeof(vals)) == 0;
+    }
+};
+
+}  // namespace
+
+struct sbt_handle {
+    sbt_config cfg;
+    DevConfig C;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    Arena plain_arena, pers_arena, stage_arena, host_arena, misc_arena;
+    int tuned_threads = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key{};
+    bool have_key = false;
+    int launches_last = 0;
+};
+
+namespace {
+
+sbt_status fail(sbt_handle* h, sbt_status st, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return st;
+}
+
+sbt_status cuda_fail(sbt_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, SBT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int default_threads(const sbt_handle* h, bool batched)
+{
+    if (h->cfg.threads_per_block) return h->cfg.threads_per_block;
+    if (batched && h->tuned_threads) return h->tuned_threads;
+    return 128;
+}
+
+sbt_status check_inputs(sbt_handle* h, const float* x, const float* y, const float* z,
+                        const int32_t* module, const int32_t* offsets, int32_t n_events,
+                        int32_t n_hits, const sbt_tracks* out)
+{
+    if (!h) return SBT_ERR_ARG;
+    if (n_events < 0 || n_hits < 0) return fail(h, SBT_ERR_ARG, "negative size");
+    if (!offsets) return fail(h, SBT_ERR_ARG, "event_offsets is NULL");
+    if (n_hits > 0 && (!x || !y || !z || !module)) return fail(h, SBT_ERR_ARG, "hit array is NULL");
+    if (out) {
+        if (!out->track_offsets || !out->hit_offsets || !out->event_status || !out->counts)
+            return fail(h, SBT_ERR_ARG, "output array is NULL");
+        if (out->cap_tracks < 0 || out->cap_hits < 0) return fail(h, SBT_ERR_ARG, "negative capacity");
+        if ((out->cap_tracks > 0 && (!out->params || !out->chi2 || !out->ndof)) ||
+            (out->cap_hits > 0 && !out->track_hits))
+            return fail(h, SBT_ERR_ARG, "output array is NULL");
+    }
+    return SBT_OK;
+}
+
+Inputs make_inputs(const float* x, const float* y, const float* z, const int32_t* module,
+                   const int32_t* offsets, int32_t n_events, int32_t n_hits)
+{
+    Inputs in;
+    in.x = x;
+    in.y = y;
+    in.z = z;
+    in.module = module;
+    in.offsets = offsets;
+    in.n_events = n_events;
+    in.n_hits = n_hits;
+    return in;
+}
+
+sbt_status ensure_staging(sbt_handle* h, int64_t n_hits, int64_t n_events, Staging* S)
+{
+    size_t need = carve_staging(nullptr, n_hits, n_events, nullptr);
+    cudaError_t e = h->stage_arena.reserve(need);
+    if (e != cudaSuccess) return cuda_fail(h, e, "staging allocation");
+    carve_staging(h->stage_arena.base, n_hits, n_events, S);
+    return SBT_OK;
+}
+
+int persistent_blocks(sbt_handle* h, int threads)
+{
+    int per_sm = persistent_blocks_per_sm(h->C, threads);
+    return std::max(per_sm, 1) * h->sm_count;
+}
+
+sbt_status ensure_persistent(sbt_handle* h, int blocks, Work* W)
+{
+    int64_t hits = (int64_t)blocks * h->C.nmax;
+    size_t need = carve_work(nullptr, hits, blocks, nullptr);
+    cudaError_t e = h->pers_arena.reserve(need);
+    if (e != cudaSuccess) return cuda_fail(h, e, "persistent workspace allocation");
+    carve_work(h->pers_arena.base, hits, blocks, W);
+    return SBT_OK;
+}
+
+// Enqueue the batched sequence (order, persistent search, scan, consolidation).
+sbt_status enqueue_batched(sbt_handle* h, const Inputs& in, const Staging& S, const Work& W,
+                           const sbt_tracks& out, int threads, int blocks, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(S.queue, 0, 4 * sizeof(int32_t), st);
+    if (e == cudaSuccess && in.n_events > 0) e = launch_order(in, S, st);
+    if (e == cudaSuccess && in.n_events > 0)
+        e = launch_persistent(h->C, in, W, S, out, threads, std::min(blocks, in.n_events), st);
+    if (e == cudaSuccess) e = launch_finish(h->C, in, S, out, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batched launch");
+    return SBT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sbt_status sbt_default_config(sbt_config* out)
+{
+    if (!out) return SBT_ERR_ARG;
+    out->k_doublets = 4;
+    out->max_scatter_seed = 0.04f;
+    out->max_scatter_follow = 0.04f;
+    out->max_chi2_tracklet = 20.0f;
+    out->hit_sigma = 0.012f;
+    out->max_hits_per_event = 16384;
+    out->max_forming_tracks = 0;
+    out->threads_per_block = 0;
+    return SBT_OK;
+}
+
+sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_handle** out)
+{
+    if (!out || !geometry || !geometry->module_z) {
+        g_create_error = "NULL argument";
+        return SBT_ERR_ARG;
+    }
+    *out = nullptr;
+    if (geometry->n_modules < 3 || geometry->n_modules > kMaxModules) {
+        g_create_error = "n_modules must be in [3, 64]";
+        return SBT_ERR_ARG;
+    }
+    sbt_config c;
+    if (cfg)
+        c = *cfg;
+    else
+        sbt_default_config(&c);
+    if (c.k_doublets < 1 || c.max_hits_per_event < 1 || c.max_hits_per_event > kMaxHitsPerEvent ||
+        c.max_forming_tracks < 0 || !(c.hit_sigma > 0.0f) ||
+        (c.threads_per_block != 0 && c.threads_per_block != 64 && c.threads_per_block != 128 &&
+         c.threads_per_block != 256)) {
+        g_create_error = "invalid configuration";
+        return SBT_ERR_ARG;
+    }
+    sbt_handle* h = new sbt_handle();
+    h->cfg = c;
+    std::memset(&h->C, 0, sizeof(h->C));
+    h->C.M = geometry->n_modules;
+    for (int m = 0; m < h->C.M; m++) h->C.module_z[m] = geometry->module_z[m];
+    h->C.K = c.k_doublets;
+    h->C.S_seed = c.max_scatter_seed;
+    h->C.S_follow = c.max_scatter_follow;
+    h->C.C3 = c.max_chi2_tracklet;
+    h->C.sigma = c.hit_sigma;
+    h->C.nmax = c.max_hits_per_event;
+    h->C.fcap = c.max_forming_tracks ? c.max_forming_tracks : std::max(256, c.max_hits_per_event / 16);
+    if (h->C.fcap > 65535) h->C.fcap = 65535;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    int max_optin = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
+        delete h;
+        return SBT_ERR_CUDA;
+    }
+    if (smem_bytes(h->C.nmax, h->C.fcap, 256) > (size_t)max_optin) {
+        g_create_error = "max_hits_per_event / max_forming_tracks exceed shared memory";
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        delete h;
+        return SBT_ERR_ARG;
+    }
+    *out = h;
+    return SBT_OK;
+}
+
+sbt_status sbt_destroy(sbt_handle* h)
+{
+    if (!h) return SBT_ERR_ARG;
+    cudaDeviceSynchronize();
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->plain_arena.release();
+    h->pers_arena.release();
+    h->stage_arena.release();
+    h->host_arena.release();
+    h->misc_arena.release();
+    delete h;
+    return SBT_OK;
+}
+
+const char* sbt_last_error(const sbt_handle* h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+sbt_status sbt_reconstruct(sbt_handle* h, const float* x, const float* y, const float* z,
+                           const int32_t* module, const int32_t* event_offsets, int32_t n_events,
+                           int32_t n_hits, const sbt_tracks* out, void* stream)
+{
+    sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, out);
+    if (st != SBT_OK || !out) return st != SBT_OK ? st : SBT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Staging S;
+    if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
+    size_t need = carve_work(nullptr, n_hits, n_events, nullptr);
+    cudaError_t e = h->plain_arena.reserve(need);
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace allocation");
+    Work W;
+    carve_work(h->plain_arena.base, n_hits, n_events, &W);
+    Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
+    e = launch_plain(h->C, in, W, S, *out, default_threads(h, false), s);
+    if (e == cudaSuccess) e = launch_finish(h->C, in, S, *out, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "plain launch");
+    h->launches_last = n_events > 0 ? 3 : 1;
+    return SBT_OK;
+}
+
+sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y, const float* z,
+                                   const int32_t* module, const int32_t* event_offsets,
+                                   int32_t n_events, int32_t n_hits, const sbt_tracks* out,
+                                   void* stream)
+{
+    sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, out);
+    if (st != SBT_OK || !out) return st != SBT_OK ? st : SBT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = default_threads(h, true);
+    const int blocks = persistent_blocks(h, threads);
+    Staging S;
+    Work W;
+    const void* old_stage = h->stage_arena.base;
+    const void* old_pers = h->pers_arena.base;
+    if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
+    if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) return st;
+    GraphKey k{};
+    const void* ptrs[13] = {x, y, z, module, event_offsets, out->track_offsets, out->hit_offsets,
+                            out->track_hits, out->params, out->chi2, out->ndof, out->event_status,
+                            out->counts};
+    std::memcpy(k.ptrs, ptrs, sizeof(ptrs));
+    k.vals[0] = n_events;
+    k.vals[1] = n_hits;
+    k.vals[2] = out->cap_tracks;
+    k.vals[3] = out->cap_hits;
+    k.vals[4] = threads;
+    k.vals[5] = blocks;
+    const bool moved = old_stage != h->stage_arena.base || old_pers != h->pers_arena.base;
+    if (!h->exec || !h->have_key || moved || !(k == h->key)) {
+        if (h->exec) {
+            cudaGraphExecDestroy(h->exec);
+            h->exec = nullptr;
+        }
+        h->have_key = false;
+        Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture begin");
+        st = enqueue_batched(h, in, S, W, *out, threads, blocks, h->cap_stream);
+        e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (st != SBT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture end");
+        e = cudaGraphInstantiate(&h->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->exec = nullptr;
+            return cuda_fail(h, e, "graph instantiate");
+        }
+        h->key = k;
+        h->have_key = true;
+    }
+    cudaError_t e = cudaGraphLaunch(h->exec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    h->launches_last = n_events > 0 ? 4 : 2;
+    return SBT_OK;
+}
+
+sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, const float* z,
+                                const int32_t* module, const int32_t* event_offsets,
+                                int32_t n_events, int32_t n_hits, const sbt_tracks* oh,
+                                void* stream)
+{
+    sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, oh);
+    if (st != SBT_OK || !oh) return st != SBT_OK ? st : SBT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // device copies of the inputs and full-capacity outputs
+    const int64_t H = n_hits, E = n_events;
+    const int64_t capT = H / 3 + 1, capH = H + 1;
+    Carver c0(nullptr);
+    auto layout = [&](Carver& c, float** dx, float** dy, float** dz, int32_t** dm, int32_t** doff,
+                      sbt_tracks* d) {
+        *dx = c.take<float>(H);
+        *dy = c.take<float>(H);
+        *dz = c.take<float>(H);
+        *dm = c.take<int32_t>(H);
+        *doff = c.take<int32_t>(E + 1);
+        d->track_offsets = c.take<int32_t>(E + 1);
+        d->hit_offsets = c.take<int32_t>(capT + 1);
+        d->track_hits = c.take<int32_t>(capH);
+        d->params = c.take<float>(4 * capT);
+        d->chi2 = c.take<float>(capT);
+        d->ndof = c.take<int32_t>(capT);
+        d->event_status = c.take<int32_t>(E);
+        d->counts = c.take<int32_t>(4);
+        d->cap_tracks = (int32_t)capT;
+        d->cap_hits = (int32_t)capH;
+    };
+    float *dx, *dy, *dz;
+    int32_t *dm, *doff;
+    sbt_tracks d;
+    layout(c0, &dx, &dy, &dz, &dm, &doff, &d);
+    cudaError_t e = h->host_arena.reserve(c0.off + 256);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host-path allocation");
+    Carver c1(h->host_arena.base);
+    layout(c1, &dx, &dy, &dz, &dm, &doff, &d);
+    e = cudaMemcpyAsync(dx, x, sizeof(float) * H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, sizeof(float) * H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z, sizeof(float) * H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dm, module, sizeof(int32_t) * H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(doff, event_offsets, sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
+    st = sbt_reconstruct_batched(h, dx, dy, dz, dm, doff, n_events, n_hits, &d, stream);
+    if (st != SBT_OK) return st;
+    int32_t counts[4];
+    e = cudaMemcpyAsync(counts, d.counts, sizeof(counts), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "count copy");
+    const int64_t T = counts[0], HH = counts[1];
+    std::memcpy(oh->counts, counts, sizeof(counts));
+    if (T > oh->cap_tracks || HH > oh->cap_hits) oh->counts[2] = SBT_ERR_CAPACITY;
+    e = cudaMemcpyAsync(oh->track_offsets, d.track_offsets, sizeof(int32_t) * (E + 1),
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(oh->event_status, d.event_status, sizeof(int32_t) * E,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && oh->counts[2] == SBT_OK) {
+        e = cudaMemcpyAsync(oh->hit_offsets, d.hit_offsets, sizeof(int32_t) * (T + 1),
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && HH > 0)
+            e = cudaMemcpyAsync(oh->track_hits, d.track_hits, sizeof(int32_t) * HH,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && T > 0)
+            e = cudaMemcpyAsync(oh->params, d.params, sizeof(float) * 4 * T, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && T > 0)
+            e = cudaMemcpyAsync(oh->chi2, d.chi2, sizeof(float) * T, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && T > 0)
+            e = cudaMemcpyAsync(oh->ndof, d.ndof, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "output copy");
+    return SBT_OK;
+}
+
+sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const float* z,
+                        const int32_t* module, const int32_t* event_offsets, int32_t n_events,
+                        int32_t n_hits, int32_t* chosen, void* stream)
+{
+    sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, nullptr);
+    if (st != SBT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Staging S;
+    if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
+    cudaError_t e = h->misc_arena.reserve(sizeof(int32_t) * ((size_t)n_events + 8));
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune allocation");
+    sbt_tracks scratch_out;
+    std::memset(&scratch_out, 0, sizeof(scratch_out));
+    scratch_out.event_status = (int32_t*)h->misc_arena.base;
+    Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best_ms = 1e30f;
+    int best = 128;
+    const int cands[3] = {64, 128, 256};
+    for (int threads : cands) {
+        const int blocks = persistent_blocks(h, threads);
+        Work W;
+        if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) break;
+        float tot = 0.0f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+            e = cudaMemsetAsync(S.queue, 0, 16, s);
+            if (e == cudaSuccess) e = launch_order(in, S, s);
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            if (e == cudaSuccess)
+                e = launch_persistent(h->C, in, W, S, scratch_out, threads,
+                                      std::min(blocks, std::max(n_events, 1)), s);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0) tot += ms;  // first repetition is warm-up
+        }
+        if (e != cudaSuccess) break;
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = threads;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != SBT_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+    h->tuned_threads = best;
+    if (chosen) *chosen = best;
+    return SBT_OK;
+}
+
+sbt_status sbt_fit_adjoint(sbt_handle* h, const float* x, const float* y, const float* z,
+                           const int32_t* module, int32_t n_hits, const int32_t* hit_offsets,
+                           const int32_t* track_hits, int32_t n_tracks, const double* align,
+                           double* chi2_sum, double* grad, void* stream)
+{
+    if (!h) return SBT_ERR_ARG;
+    if (n_hits < 0 || n_tracks < 0) return fail(h, SBT_ERR_ARG, "negative size");
+    if (!hit_offsets || !align || !chi2_sum || (n_tracks > 0 && (!track_hits || !x || !y || !z || !module)))
+        return fail(h, SBT_ERR_ARG, "NULL argument");
+    AdjointWork W;
+    W.blocks = adjoint_blocks();
+    size_t need = sizeof(double) * (size_t)W.blocks * (6 * h->C.M + 1);
+    cudaError_t e = h->misc_arena.reserve(std::max(need, h->misc_arena.bytes));
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint allocation");
+    W.partial = (double*)h->misc_arena.base;
+    Inputs in = make_inputs(x, y, z, module, nullptr, 0, n_hits);
+    e = launch_adjoint(h->C, in, hit_offsets, track_hits, n_tracks, align, chi2_sum, grad, W,
+                       (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint launch");
+    return SBT_OK;
+}
+
+sbt_status sbt_debug_sort(sbt_handle* h, const float* x, const float* y, const int32_t* module,
+                          const int32_t* event_offsets, int32_t n_events, int32_t n_hits,
+                          uint16_t* phi16, int32_t* perm, int32_t* module_offsets, void* stream)
+{
+    sbt_status st = check_inputs(h, x, y, x, module, event_offsets, n_events, n_hits, nullptr);
+    if (st != SBT_OK) return st;
+    if (!phi16 || !perm || !module_offsets) return fail(h, SBT_ERR_ARG, "NULL output");
+    size_t need = carve_work(nullptr, n_hits, n_events, nullptr);
+    cudaError_t e = h->plain_arena.reserve(need);
+    if (e == cudaSuccess) e = h->misc_arena.reserve(std::max(sizeof(int32_t) * ((size_t)n_events + 8), h->misc_arena.bytes));
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace allocation");
+    Work W;
+    carve_work(h->plain_arena.base, n_hits, n_events, &W);
+    Inputs in = make_inputs(x, y, x, module, event_offsets, n_events, n_hits);
+    e = launch_debug_sort(h->C, in, W, phi16, perm, module_offsets, (int32_t*)h->misc_arena.base,
+                          default_threads(h, false), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "debug sort launch");
+    return SBT_OK;
+}
+
+sbt_status sbt_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y || !out))) return SBT_ERR_ARG;
+    cudaError_t e = launch_debug_phi16(x, y, n, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? SBT_OK : SBT_ERR_CUDA;
+}
+
+sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, const float* z,
+                               const int32_t* module, const int32_t* event_offsets,
+                               int32_t n_events, int32_t n_hits, const sbt_tracks* out, int32_t reps,
+                               float* ms, void* stream)
+{
+    sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, out);
+    if (st != SBT_OK || !out || !ms || reps < 1) return st != SBT_OK ? st : fail(h, SBT_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = default_threads(h, true);
+    const int blocks = persistent_blocks(h, threads);
+    Staging S;
+    Work W;
+    if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
+    if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) return st;
+    // invalidate the graph cache: the arenas may have moved
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+        h->have_key = false;
+    }
+    Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; i++) cudaEventCreate(&ev[i]);
+    double acc[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; r++) {
+        e = cudaMemsetAsync(S.queue, 0, 16, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess && n_events > 0) e = launch_order(in, S, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess && n_events > 0)
+            e = launch_persistent(h->C, in, W, S, *out, threads, std::min(blocks, n_events), s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
+        if (e == cudaSuccess) e = launch_scan(in, S, *out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
+        if (e == cudaSuccess) e = launch_consolidate(h->C, in, S, *out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+        for (int k = 0; k < 4 && e == cudaSuccess; k++) {
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (int i = 0; i < 5; i++) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "profile");
+    for (int k = 0; k < 4; k++) ms[k] = (float)(acc[k] / reps);
+    return SBT_OK;
+}
+
+/* Number of kernels the last reconstruction call enqueued (for launch accounting). */
+int32_t sbt_last_launch_count(const sbt_handle* h) { return h ? h->launches_last : 0; }
+
+}  // extern "C"

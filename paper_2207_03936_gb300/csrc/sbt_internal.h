@@ -1,0 +1,102 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sbt.h"
+
+namespace sbt {
+
+constexpr int kMaxModules = 64;
+constexpr int kMaxHitsPerEvent = 65533;  // event-local indices are uint16; 0xFFFF and 0xFFFE are markers
+
+// Method constants and per-event capacities, passed to kernels by value.
+struct DevConfig {
+    int M;
+    float module_z[kMaxModules];
+    int K;
+    float S_seed, S_follow, C3, sigma;
+    int nmax;  // max hits per event
+    int fcap;  // forming-track buffer entries
+};
+
+struct Inputs {
+    const float* x;
+    const float* y;
+    const float* z;
+    const int32_t* module;
+    const int32_t* offsets;
+    int32_t n_events;
+    int32_t n_hits;
+};
+
+// Per-region scratch (a region is an event in the plain launch, a resident
+// block in the persistent launch).  Region r with hit base hb and capacity
+// cap owns per-hit arrays [hb, hb + cap), tracklets from hb/4 + r (cap/4 + 1
+// entries) and final-track records from hb/3 + r (cap/3 + 1 entries).
+struct Work {
+    float4* coords;              // sorted (x, y, z, input index as int bits)
+    uint32_t* keys;              // (module << 16 | phi16) by input index
+    uint16_t* idxA;              // radix ping buffer; canonical-order marks afterwards
+    uint16_t* idxB;              // radix pong buffer; final sorted order
+    uint16_t* prev;              // previous hit of a track, by sorted position
+    unsigned long long* claim;   // hit claims (tagged keys), by sorted position
+    unsigned long long* tracklets;
+    uint32_t* tl_q;
+    uint32_t* finals;            // last hit | nhits << 16
+    int32_t* fin_rank;
+    int32_t* fin_start;
+};
+
+// Per-event staging of the search output, consumed by the consolidation.
+struct Staging {
+    int32_t* hits;        // [n_hits]: event e writes from event_offsets[e]
+    uint8_t* len;         // [n_hits / 3 + n_events + 1]: event e from off/3 + e
+    int32_t* ev_ntracks;  // [n_events]
+    int32_t* ev_nhits;    // [n_events]
+    int32_t* track_base;  // [n_events]
+    int32_t* hit_base;    // [n_events]
+    int32_t* order;       // [n_events] processing order of the persistent launch
+    int32_t* queue;       // [4]      work-queue head
+};
+
+// Sizes of the scratch arrays for `hits` hit slots over `regions` regions.
+inline int64_t tracklet_entries(int64_t hits, int64_t regions) { return hits / 4 + regions + 1; }
+inline int64_t final_entries(int64_t hits, int64_t regions) { return hits / 3 + regions + 1; }
+
+size_t smem_bytes(int nmax, int fcap, int threads);
+
+// Launchers (sbt_reco.cu).  All asynchronous on `stream`.
+cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Work& W, const Staging& S,
+                         const sbt_tracks& out, int threads, cudaStream_t stream);
+cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream);
+cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Work& W,
+                              const Staging& S, const sbt_tracks& out, int threads, int blocks,
+                              cudaStream_t stream);
+cudaError_t launch_finish(const DevConfig& C, const Inputs& in, const Staging& S,
+                          const sbt_tracks& out, cudaStream_t stream);
+cudaError_t launch_scan(const Inputs& in, const Staging& S, const sbt_tracks& out,
+                        cudaStream_t stream);
+cudaError_t launch_consolidate(const DevConfig& C, const Inputs& in, const Staging& S,
+                               const sbt_tracks& out, cudaStream_t stream);
+cudaError_t launch_debug_sort(const DevConfig& C, const Inputs& in, const Work& W,
+                              uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
+                              int32_t* status, int threads, cudaStream_t stream);
+cudaError_t launch_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out,
+                               cudaStream_t stream);
+int persistent_blocks_per_sm(const DevConfig& C, int threads);
+int plain_kernel_count();
+
+// Adjoint (sbt_adjoint.cu).
+struct AdjointWork {
+    double* partial;   // [blocks * (6 M + 1)]
+    int blocks;
+};
+cudaError_t launch_adjoint(const DevConfig& C, const Inputs& in, const int32_t* hit_offsets,
+                           const int32_t* track_hits, int32_t n_tracks, const double* align,
+                           double* chi2_sum, double* grad, const AdjointWork& W,
+                           cudaStream_t stream);
+int adjoint_blocks();
+
+}  // namespace sbt

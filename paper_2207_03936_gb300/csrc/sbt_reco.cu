@@ -1,0 +1,1167 @@
+// Search-by-triplet reconstruction kernels for sm_103a.
+//
+// One thread block reconstructs one event (Table 1 of the paper: events map
+// to blocks, hits and forming tracks to threads).  Per event:
+//   1. phi16 of every hit and a stable LSD radix sort of (module, phi16) in
+//      three passes (section "Sort by phi"); sorted hits are gathered into
+//      an AoS float4 array (x, y, z, input index);
+//   2. for every module triplet (s, s+1, s+2): seeding over the unflagged
+//      middle hits, then following of every forming track to module s+3 with
+//      one-round claims on the hits, flags, and termination after two misses
+//      (section "Track seeding and track following"); barriers separate the
+//      stages as the paper's flagged-hits dependency requires;
+//   3. the tracklet filter (section "Tracklet filter");
+//   4. canonical ordering of the tracks by smallest input hit index and
+//      staging of their hit lists.
+// A device-wide scan and a consolidation kernel then build the CSR output
+// and fit every track (section "Results", data consolidation).
+//
+// Decision arithmetic is fp32 with every operation rounded as written
+// (explicit _rn intrinsics, no contraction), so that the result is the
+// exact track set of the plain definition.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "sbt_internal.h"
+
+namespace sbt {
+
+constexpr uint16_t kNone = 0xFFFFu;
+constexpr uint16_t kDead = 0xFFFEu;
+
+// ------------------------------------------------------------------ phi ---
+
+// 2-argument arctangent: octant reduction and the degree-9 odd polynomial of
+// the Hastings form (Abramowitz & Stegun 4.4.48), every operation rounded.
+__device__ __forceinline__ float atan2_sbt(float y, float x)
+{
+    const float a1 = 0.9998660f, a3 = -0.3302995f, a5 = 0.1801410f;
+    const float a7 = -0.0851330f, a9 = 0.0208351f;
+    float ax = fabsf(x);
+    float ay = fabsf(y);
+    float mx = ax > ay ? ax : ay;
+    float mn = ax > ay ? ay : ax;
+    if (mx == 0.0f) return 0.0f;
+    float t = __fdiv_rn(mn, mx);
+    float t2 = __fmul_rn(t, t);
+    float p = a9;
+    p = __fadd_rn(__fmul_rn(p, t2), a7);
+    p = __fadd_rn(__fmul_rn(p, t2), a5);
+    p = __fadd_rn(__fmul_rn(p, t2), a3);
+    p = __fadd_rn(__fmul_rn(p, t2), a1);
+    p = __fmul_rn(p, t);
+    if (ay > ax) p = __fsub_rn(1.5707963267948966f, p);
+    if (x < 0.0f) p = __fsub_rn(3.14159265358979323846f, p);
+    if (y < 0.0f) p = -p;
+    return p;
+}
+
+// [-pi, pi] onto the unsigned 16-bit range, modulo 2^16.
+__device__ __forceinline__ uint32_t phi16_of(float x, float y)
+{
+    float a = atan2_sbt(y, x);
+    int q = __float2int_rn(__fmul_rn(a, 10430.378350470453f));
+    return (uint32_t)q & 0xFFFFu;
+}
+
+__device__ __forceinline__ int phi_dist(uint32_t u, uint32_t v)
+{
+    int d1 = (int)((u - v) & 0xFFFFu);
+    int d2 = (int)((v - u) & 0xFFFFu);
+    return d1 < d2 ? d1 : d2;
+}
+
+// First position in phi[0, n) with phi >= v.
+__device__ __forceinline__ int lower_bound16(const uint16_t* phi, int n, uint32_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((uint32_t)phi[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Straight-line extrapolation of (a, c) to the plane z = zt.
+__device__ __forceinline__ void extrapolate(float4 A, float4 Cc, float zt, float& xp, float& yp)
+{
+    float dz = __fsub_rn(Cc.z, A.z);
+    float tz = __fdiv_rn(__fsub_rn(zt, Cc.z), dz);
+    xp = __fadd_rn(Cc.x, __fmul_rn(__fsub_rn(Cc.x, A.x), tz));
+    yp = __fadd_rn(Cc.y, __fmul_rn(__fsub_rn(Cc.y, A.y), tz));
+}
+
+__device__ __forceinline__ float scatter_of(float4 B, float xp, float yp)
+{
+    float dx = __fsub_rn(B.x, xp);
+    float dy = __fsub_rn(B.y, yp);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+// Least-squares straight line through n hits (get(i) -> float3 in hit
+// order): params (x0, y0, tx, ty) at z = 0 and chi2 = residual sum / sigma^2.
+template <class Get>
+__device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* params, float* chi2)
+{
+    float nf = (float)n;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int i = 0; i < n; i++) {
+        float3 h = get(i);
+        sx = __fadd_rn(sx, h.x);
+        sy = __fadd_rn(sy, h.y);
+        sz = __fadd_rn(sz, h.z);
+    }
+    float xm = __fdiv_rn(sx, nf), ym = __fdiv_rn(sy, nf), zm = __fdiv_rn(sz, nf);
+    float szz = 0.0f, szx = 0.0f, szy = 0.0f;
+    for (int i = 0; i < n; i++) {
+        float3 h = get(i);
+        float dz = __fsub_rn(h.z, zm);
+        szz = __fadd_rn(szz, __fmul_rn(dz, dz));
+        szx = __fadd_rn(szx, __fmul_rn(dz, __fsub_rn(h.x, xm)));
+        szy = __fadd_rn(szy, __fmul_rn(dz, __fsub_rn(h.y, ym)));
+    }
+    float tx = __fdiv_rn(szx, szz);
+    float ty = __fdiv_rn(szy, szz);
+    float s = 0.0f;
+    for (int i = 0; i < n; i++) {
+        float3 h = get(i);
+        float dz = __fsub_rn(h.z, zm);
+        float rx = __fsub_rn(__fsub_rn(h.x, xm), __fmul_rn(tx, dz));
+        float ry = __fsub_rn(__fsub_rn(h.y, ym), __fmul_rn(ty, dz));
+        s = __fadd_rn(s, __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)));
+    }
+    if (params) {
+        params[0] = __fsub_rn(xm, __fmul_rn(tx, zm));
+        params[1] = __fsub_rn(ym, __fmul_rn(ty, zm));
+        params[2] = tx;
+        params[3] = ty;
+    }
+    *chi2 = __fdiv_rn(s, __fmul_rn(sigma, sigma));
+}
+
+// ------------------------------------------------------- shared layout ---
+
+enum Misc { kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kTotH = 6, kMiscN = 32 };
+
+struct Smem {
+    uint16_t* phi;
+    uint8_t* flag;
+    int* modoff;
+    uint16_t* fh[2][3];
+    uint16_t* fkey[2];
+    uint8_t* fnh[2];
+    uint8_t* fsk[2];
+    uint16_t* fcand;
+    float* fsc;
+    int* hist;  // radix histograms, aliases the forming buffers
+    int* misc;
+    int* tot;   // [256]
+    int* base;  // [256]
+    int* wsum;  // [33]
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+struct Plan {
+    size_t phi, flag, modoff, forming, misc, tot, base, wsum, total;
+};
+
+__host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
+{
+    Plan p;
+    size_t o = 0;
+    p.phi = o;      o = align16(o + 2 * (size_t)nmax);
+    p.flag = o;     o = align16(o + (size_t)nmax);
+    p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
+    size_t form = 26 * (size_t)fcap;
+    size_t hist = 4 * 256 * (size_t)(threads / 32);
+    p.forming = o;  o = align16(o + (form > hist ? form : hist));
+    p.misc = o;     o = align16(o + 4 * kMiscN);
+    p.tot = o;      o = align16(o + 4 * 256);
+    p.base = o;     o = align16(o + 4 * 256);
+    p.wsum = o;     o = align16(o + 4 * 40);
+    p.total = o;
+    return p;
+}
+
+size_t smem_bytes(int nmax, int fcap, int threads) { return make_plan(nmax, fcap, threads).total; }
+
+__device__ inline Smem carve(unsigned char* raw, int nmax, int fcap, int threads)
+{
+    Plan p = make_plan(nmax, fcap, threads);
+    Smem S;
+    S.phi = (uint16_t*)(raw + p.phi);
+    S.flag = raw + p.flag;
+    S.modoff = (int*)(raw + p.modoff);
+    unsigned char* f = raw + p.forming;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) {
+            S.fh[b][k] = (uint16_t*)f;
+            f += 2 * (size_t)fcap;
+        }
+    for (int b = 0; b < 2; b++) {
+        S.fkey[b] = (uint16_t*)f;
+        f += 2 * (size_t)fcap;
+    }
+    S.fcand = (uint16_t*)f;
+    f += 2 * (size_t)fcap;
+    S.fsc = (float*)f;
+    f += 4 * (size_t)fcap;
+    for (int b = 0; b < 2; b++) {
+        S.fnh[b] = f;
+        f += fcap;
+        S.fsk[b] = f;
+        f += fcap;
+    }
+    S.hist = (int*)(raw + p.forming);
+    S.misc = (int*)(raw + p.misc);
+    S.tot = (int*)(raw + p.tot);
+    S.base = (int*)(raw + p.base);
+    S.wsum = (int*)(raw + p.wsum);
+    return S;
+}
+
+struct Region {
+    float4* coords;
+    uint32_t* keys;
+    uint16_t* idxA;
+    uint16_t* idxB;
+    uint16_t* prev;
+    unsigned long long* claim;
+    unsigned long long* tracklets;
+    uint32_t* tl_q;
+    int lcap;
+    uint32_t* finals;
+    int32_t* fin_rank;
+    int32_t* fin_start;
+};
+
+__device__ inline Region region_of(const Work& W, int64_t hb, int64_t r, int cap)
+{
+    Region R;
+    R.coords = W.coords + hb;
+    R.keys = W.keys + hb;
+    R.idxA = W.idxA + hb;
+    R.idxB = W.idxB + hb;
+    R.prev = W.prev + hb;
+    R.claim = W.claim + hb;
+    R.tracklets = W.tracklets + hb / 4 + r;
+    R.tl_q = W.tl_q + hb / 4 + r;
+    R.lcap = cap / 4 + 1;
+    R.finals = W.finals + hb / 3 + r;
+    R.fin_rank = W.fin_rank + hb / 3 + r;
+    R.fin_start = W.fin_start + hb / 3 + r;
+    return R;
+}
+
+// Exclusive block scan of one int per thread; returns the prefix, *total the
+// sum.  wsum needs 33 entries.
+template <int NT>
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NT / 32 ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < NT / 32) wsum[lane] = wi - w;
+        if (lane == NT / 32 - 1) wsum[32] = wi;
+    }
+    __syncthreads();
+    int res = wsum[warp] + incl - v;
+    *total = wsum[32];
+    __syncthreads();
+    return res;
+}
+
+// -------------------------------------------------------------- sorting ---
+
+// One stable counting pass over `bits` bits of keys[src[i]] >> shift.
+// Warp w owns the contiguous chunk w of the input; ranks among equal digits
+// inside a warp come from match/popc, so the pass is stable.
+template <int NT>
+__device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* dst, int n,
+                           int shift, int bits, const Smem& S, int* modoff_out, int M)
+{
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nd = 1 << bits;
+    const unsigned lt = (1u << lane) - 1u;
+    int* hist = S.hist;
+    for (int k = tid; k < NW * 256; k += NT) hist[k] = 0;
+    __syncthreads();
+    const int chunk = (n + NW - 1) / NW;
+    const int beg = warp * chunk;
+    const int end = min(n, beg + chunk);
+    for (int b = beg; b < end; b += 32) {
+        int j = b + lane;
+        bool v = j < end;
+        unsigned d = v ? ((keys[src[j]] >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
+        unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (v && lane == __ffs(peers) - 1) hist[warp * 256 + d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = tid; d < nd; d += NT) {
+        int s = 0;
+        for (int w = 0; w < NW; w++) s += hist[w * 256 + d];
+        S.tot[d] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int per = nd / 32;
+        int s = 0;
+        for (int k = 0; k < per; k++) s += S.tot[lane * per + k];
+        int incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int ex = incl - s;
+        for (int k = 0; k < per; k++) {
+            S.base[lane * per + k] = ex;
+            ex += S.tot[lane * per + k];
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < nd; d += NT) {
+        int b = S.base[d];
+        for (int w = 0; w < NW; w++) {
+            int h = hist[w * 256 + d];
+            hist[w * 256 + d] = b;
+            b += h;
+        }
+    }
+    if (modoff_out)
+        for (int d = tid; d <= M; d += NT) modoff_out[d] = d < M ? S.base[d] : n;
+    __syncthreads();
+    for (int b = beg; b < end; b += 32) {
+        int j = b + lane;
+        bool v = j < end;
+        unsigned d = v ? ((keys[src[j]] >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
+        unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        int pos = v ? hist[warp * 256 + d] + __popc(peers & lt) : 0;
+        __syncwarp();
+        if (v) {
+            dst[pos] = src[j];
+            if (lane == __ffs(peers) - 1) hist[warp * 256 + d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// Sort stage: keys, radix passes, gather.  Returns false (uniformly) when a
+// module id is out of range.
+template <int NT>
+__device__ bool sort_stage(const DevConfig& C, const Inputs& in, int off, int n, const Region& R,
+                           const Smem& S)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) S.misc[kErr] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += NT) {
+        int m = in.module[off + i];
+        if (m < 0 || m >= C.M) {
+            S.misc[kErr] = SBT_ERR_ARG;
+            m = 0;
+        }
+        R.keys[i] = ((uint32_t)m << 16) | phi16_of(in.x[off + i], in.y[off + i]);
+        R.idxA[i] = (uint16_t)i;
+    }
+    __syncthreads();
+    if (S.misc[kErr]) return false;
+    radix_pass<NT>(R.keys, R.idxA, R.idxB, n, 0, 8, S, nullptr, C.M);
+    radix_pass<NT>(R.keys, R.idxB, R.idxA, n, 8, 8, S, nullptr, C.M);
+    radix_pass<NT>(R.keys, R.idxA, R.idxB, n, 16, 6, S, S.modoff, C.M);
+    for (int p = tid; p < n; p += NT) {
+        int i = R.idxB[p];
+        S.phi[p] = (uint16_t)(R.keys[i] & 0xFFFFu);
+        S.flag[p] = 0;
+        R.coords[p] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
+        R.claim[p] = ~0ull;
+        R.idxA[p] = kNone;  // canonical-order marks
+    }
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------ seeding, following ---
+
+// Best unflagged hit on module [b0, b0 + nb) for the prediction (xp, yp)
+// with scatter < S.  Hits outside a phi window around the prediction cannot
+// pass the cut: a hit within sqrt(S) of the prediction differs from it in
+// angle by at most asin(sqrt(S) / r), bounded by tan(asin u) = sqrt(S / (r^2
+// - S)); the window adds 1/16 of that plus 16 phi16 units for the rounding
+// and arctangent error of both phi values.  Predictions near the axis scan
+// the whole module.  `better(sc, b)` orders candidates.
+template <class Better, class Take>
+__device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int b0, int nb, float xp,
+                                            float yp, float cut, Better better, Take take)
+{
+    if (nb <= 0) return;
+    float rp2 = __fadd_rn(__fmul_rn(xp, xp), __fmul_rn(yp, yp));
+    int lo_idx = 0, count = nb;
+    uint32_t lo = 0, width = 0xFFFFu;
+    bool windowed = false;
+    if (rp2 < 1.0e30f && rp2 > 4.0f * cut) {
+        float u = sqrtf(cut / (rp2 - cut));
+        float wf = u * 10430.378f * 1.0625f;
+        if (wf < 16000.0f) {
+            int W = (int)wf + 16;
+            uint32_t php = phi16_of(xp, yp);
+            lo = (php - (uint32_t)W) & 0xFFFFu;
+            width = 2u * (uint32_t)W;
+            lo_idx = lower_bound16(S.phi + b0, nb, lo);
+            windowed = true;
+        }
+    }
+    for (int k = 0; k < count; k++) {
+        int e = lo_idx + k;
+        if (e >= nb) e -= nb;
+        int b = b0 + e;
+        if (windowed && (((uint32_t)S.phi[b] - lo) & 0xFFFFu) > width) break;
+        if (S.flag[b]) continue;
+        float sc = scatter_of(R.coords[b], xp, yp);
+        if (sc < cut && better(sc, b)) take(sc, b);
+    }
+}
+
+// Seeding for middle hit c on module s+1: the unflagged hits of module s
+// nearest to c in phi (all hits at the K-th smallest distance included),
+// each extrapolated through c to module s+2, where the unflagged hit of
+// least scatter under the cut is sought; the kept triplet minimises
+// (scatter, position of a, position of b).
+__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int s, int c, int& oa,
+                         int& ob)
+{
+    const int o0 = S.modoff[s], no = S.modoff[s + 1] - o0;
+    const int i0 = S.modoff[s + 2], ni = S.modoff[s + 3] - i0;
+    if (no <= 0 || ni <= 0) return false;
+    const uint32_t phc = S.phi[c];
+    const float4 Cc = R.coords[c];
+    const float zi = C.module_z[s + 2];
+    const int j = lower_bound16(S.phi + o0, no, phc);
+    int up = j, dn = j - 1;
+    int found = 0, dK = INT_MAX;
+    bool have = false;
+    float best_sc = 0.0f;
+    int best_a = 0, best_b = 0;
+    for (int visited = 0; visited < no; visited++) {
+        int iu = up >= no ? up - no : up;
+        int id = dn < 0 ? dn + no : dn;
+        int du = phi_dist(S.phi[o0 + iu], phc);
+        int dd = phi_dist(S.phi[o0 + id], phc);
+        int a, d;
+        if (du < dd || (du == dd && iu <= id)) {
+            a = o0 + iu;
+            d = du;
+            up++;
+        } else {
+            a = o0 + id;
+            d = dd;
+            dn--;
+        }
+        if (found >= C.K && d > dK) break;
+        if (S.flag[a]) continue;
+        found++;
+        if (found == C.K) dK = d;
+        float xp, yp;
+        extrapolate(R.coords[a], Cc, zi, xp, yp);
+        scan_window(
+            S, R, i0, ni, xp, yp, C.S_seed,
+            [&](float sc, int b) {
+                return !have || sc < best_sc ||
+                       (sc == best_sc && (a < best_a || (a == best_a && b < best_b)));
+            },
+            [&](float sc, int b) {
+                have = true;
+                best_sc = sc;
+                best_a = a;
+                best_b = b;
+            });
+    }
+    if (have) {
+        oa = best_a;
+        ob = best_b;
+    }
+    return have;
+}
+
+// Following: best unflagged hit on module t for the track's last two hits.
+__device__ bool follow_best(const DevConfig& C, const Smem& S, const Region& R, int t, int h1, int h2,
+                            int& cand, float& csc)
+{
+    const int b0 = S.modoff[t], nb = S.modoff[t + 1] - b0;
+    float xp, yp;
+    extrapolate(R.coords[h1], R.coords[h2], C.module_z[t], xp, yp);
+    bool have = false;
+    float best = 0.0f;
+    int bb = 0;
+    scan_window(
+        S, R, b0, nb, xp, yp, C.S_follow,
+        [&](float sc, int b) { return !have || sc < best || (sc == best && b < bb); },
+        [&](float sc, int b) {
+            have = true;
+            best = sc;
+            bb = b;
+        });
+    cand = bb;
+    csc = best;
+    return have;
+}
+
+__device__ __forceinline__ unsigned long long claim_key(unsigned long long tag, float score, int key)
+{
+    return tag | ((unsigned long long)__float_as_uint(score) << 16) | (unsigned long long)key;
+}
+
+__device__ __forceinline__ void add_final(const Smem& S, const Region& R, int last, int nh)
+{
+    int k = atomicAdd(&S.misc[kNFin], 1);
+    R.finals[k] = (uint32_t)last | ((uint32_t)nh << 16);
+}
+
+__device__ __forceinline__ void add_tracklet(const Smem& S, const Region& R, int h0, int h1, int h2,
+                                             int key)
+{
+    int k = atomicAdd(&S.misc[kNTl], 1);
+    if (k < R.lcap)
+        R.tracklets[k] = (unsigned long long)h0 | ((unsigned long long)h1 << 16) |
+                         ((unsigned long long)h2 << 32) | ((unsigned long long)key << 48);
+    else
+        S.misc[kErr] = SBT_ERR_CAPACITY;
+}
+
+// Iterative seeding and following.  Returns false (uniformly) on overflow.
+// Claims carry a tag (64 - t) << 48 above (scatter bits, track key), so a
+// claim of an earlier step always compares larger than one of the current
+// step and the claim words need no reset between steps.
+template <int NT>
+__device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
+{
+    const int tid = threadIdx.x;
+    const int M = C.M;
+    int* misc = S.misc;
+    if (tid == 0) {
+        misc[kCnt0] = 0;
+        misc[kCnt1] = 0;
+        misc[kNFin] = 0;
+        misc[kNTl] = 0;
+        misc[kErr] = 0;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int s = 0; s + 2 <= M - 1; ++s) {
+        const int nxt = cur ^ 1;
+        if (tid == 0) misc[kCnt0 + nxt] = 0;
+        // seeding over modules (s, s+1, s+2)
+        const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
+        for (int c = c0 + tid; c < c1; c += NT) {
+            if (S.flag[c]) continue;
+            int a, b;
+            if (seed_for(C, S, R, s, c, a, b)) {
+                int slot = atomicAdd(&misc[kCnt0 + cur], 1);
+                if (slot < C.fcap) {
+                    S.fh[cur][0][slot] = (uint16_t)a;
+                    S.fh[cur][1][slot] = (uint16_t)c;
+                    S.fh[cur][2][slot] = (uint16_t)b;
+                    S.fkey[cur][slot] = (uint16_t)c;
+                    S.fnh[cur][slot] = 3;
+                    S.fsk[cur][slot] = 0;
+                } else {
+                    misc[kErr] = SBT_ERR_CAPACITY;
+                }
+            }
+        }
+        __syncthreads();
+        if (misc[kErr]) return false;
+        const int nf = misc[kCnt0 + cur];
+        const int t = s + 3;
+        if (t <= M - 1) {
+            const unsigned long long tag = (unsigned long long)(64 - t) << 48;
+            // following: candidates and claims
+            for (int f = tid; f < nf; f += NT) {
+                const int nh = S.fnh[cur][f];
+                const int h0 = S.fh[cur][0][f], h1 = S.fh[cur][1][f], h2 = S.fh[cur][2][f];
+                uint16_t cand = kNone;
+                float sc = 0.0f;
+                if (nh == 3 && (S.flag[h0] | S.flag[h1] | S.flag[h2])) {
+                    cand = kDead;
+                } else {
+                    int b;
+                    if (follow_best(C, S, R, t, h1, h2, b, sc)) {
+                        cand = (uint16_t)b;
+                        unsigned long long k = claim_key(tag, sc, S.fkey[cur][f]);
+                        atomicMin(&R.claim[b], k);
+                        if (nh == 3) {
+                            atomicMin(&R.claim[h0], k);
+                            atomicMin(&R.claim[h1], k);
+                            atomicMin(&R.claim[h2], k);
+                        }
+                    }
+                }
+                S.fcand[f] = cand;
+                S.fsc[f] = sc;
+            }
+            __syncthreads();
+            // resolution: an extension is kept when it holds every hit it claimed
+            for (int f = tid; f < nf; f += NT) {
+                const uint16_t cand = S.fcand[f];
+                if (cand == kDead) continue;
+                const int nh = S.fnh[cur][f];
+                const int h0 = S.fh[cur][0][f], h1 = S.fh[cur][1][f], h2 = S.fh[cur][2][f];
+                const int key = S.fkey[cur][f];
+                int sk = S.fsk[cur][f];
+                bool won = false;
+                if (cand != kNone) {
+                    unsigned long long k = claim_key(tag, S.fsc[f], key);
+                    won = __ldcg(&R.claim[cand]) == k;
+                    if (won && nh == 3)
+                        won = __ldcg(&R.claim[h0]) == k && __ldcg(&R.claim[h1]) == k &&
+                              __ldcg(&R.claim[h2]) == k;
+                }
+                if (won) {
+                    S.flag[cand] = 1;
+                    if (nh == 3) {
+                        S.flag[h0] = 1;
+                        S.flag[h1] = 1;
+                        S.flag[h2] = 1;
+                        R.prev[h0] = kNone;
+                        R.prev[h1] = (uint16_t)h0;
+                        R.prev[h2] = (uint16_t)h1;
+                    }
+                    R.prev[cand] = (uint16_t)h2;
+                    int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
+                    S.fh[nxt][0][slot] = (uint16_t)h1;
+                    S.fh[nxt][1][slot] = (uint16_t)h2;
+                    S.fh[nxt][2][slot] = cand;
+                    S.fkey[nxt][slot] = (uint16_t)key;
+                    S.fnh[nxt][slot] = (uint8_t)(nh + 1);
+                    S.fsk[nxt][slot] = 0;
+                } else {
+                    sk += 1;
+                    if (sk >= 2) {
+                        if (nh >= 4)
+                            add_final(S, R, h2, nh);
+                        else
+                            add_tracklet(S, R, h0, h1, h2, key);
+                    } else {
+                        int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
+                        S.fh[nxt][0][slot] = (uint16_t)h0;
+                        S.fh[nxt][1][slot] = (uint16_t)h1;
+                        S.fh[nxt][2][slot] = (uint16_t)h2;
+                        S.fkey[nxt][slot] = (uint16_t)key;
+                        S.fnh[nxt][slot] = (uint8_t)nh;
+                        S.fsk[nxt][slot] = (uint8_t)sk;
+                    }
+                }
+            }
+            __syncthreads();
+            cur = nxt;
+        } else {
+            // last iteration: every forming track is finished
+            for (int f = tid; f < nf; f += NT) {
+                const int nh = S.fnh[cur][f];
+                const int h0 = S.fh[cur][0][f], h1 = S.fh[cur][1][f], h2 = S.fh[cur][2][f];
+                if (nh >= 4)
+                    add_final(S, R, h2, nh);
+                else
+                    add_tracklet(S, R, h0, h1, h2, S.fkey[cur][f]);
+            }
+            __syncthreads();
+        }
+    }
+    return misc[kErr] == 0;
+}
+
+// Tracklet filter: three unflagged hits and chi2 < C3, then one claim round
+// among the survivors (tag 0, below every search tag).
+template <int NT>
+__device__ void tracklet_filter(const DevConfig& C, const Region& R, const Smem& S)
+{
+    const int tid = threadIdx.x;
+    const int ntl = min(S.misc[kNTl], R.lcap);
+    for (int k = tid; k < ntl; k += NT) {
+        unsigned long long v = R.tracklets[k];
+        int h[3] = {(int)(v & 0xFFFF), (int)((v >> 16) & 0xFFFF), (int)((v >> 32) & 0xFFFF)};
+        int key = (int)(v >> 48);
+        uint32_t q = 0xFFFFFFFFu;
+        if (!S.flag[h[0]] && !S.flag[h[1]] && !S.flag[h[2]]) {
+            float chi2;
+            fit_line(
+                3,
+                [&](int i) {
+                    float4 c = R.coords[h[i]];
+                    return make_float3(c.x, c.y, c.z);
+                },
+                C.sigma, nullptr, &chi2);
+            if (chi2 < C.C3) {
+                q = __float_as_uint(chi2);
+                unsigned long long kk = claim_key(0ull, chi2, key);
+                atomicMin(&R.claim[h[0]], kk);
+                atomicMin(&R.claim[h[1]], kk);
+                atomicMin(&R.claim[h[2]], kk);
+            }
+        }
+        R.tl_q[k] = q;
+    }
+    __syncthreads();
+    for (int k = tid; k < ntl; k += NT) {
+        uint32_t q = R.tl_q[k];
+        if (q == 0xFFFFFFFFu) continue;
+        unsigned long long v = R.tracklets[k];
+        int h0 = (int)(v & 0xFFFF), h1 = (int)((v >> 16) & 0xFFFF), h2 = (int)((v >> 32) & 0xFFFF);
+        unsigned long long kk = claim_key(0ull, __uint_as_float(q), (int)(v >> 48));
+        if (__ldcg(&R.claim[h0]) == kk && __ldcg(&R.claim[h1]) == kk && __ldcg(&R.claim[h2]) == kk) {
+            R.prev[h0] = kNone;
+            R.prev[h1] = (uint16_t)h0;
+            R.prev[h2] = (uint16_t)h1;
+            add_final(S, R, h2, 3);
+        }
+    }
+    __syncthreads();
+}
+
+// Canonical order (smallest input hit index) and staging of the hit lists.
+template <int NT>
+__device__ void output_stage(int e, int off, int n, const Region& R, const Smem& S,
+                             const Staging& G, const sbt_tracks& out)
+{
+    const int tid = threadIdx.x;
+    const int T = S.misc[kNFin];
+    uint16_t* mark = R.idxA;
+    for (int k = tid; k < T; k += NT) {
+        uint32_t v = R.finals[k];
+        int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
+        int mn = INT_MAX;
+        for (int j = 0; j < nh; j++) {
+            int i = __float_as_int(R.coords[q].w);
+            mn = i < mn ? i : mn;
+            q = R.prev[q];
+        }
+        mark[mn] = (uint16_t)k;
+    }
+    __syncthreads();
+    // ranks: running count of marks over input indices
+    {
+        const int chunk = (n + NT - 1) / NT;
+        const int beg = min(n, tid * chunk), end = min(n, beg + chunk);
+        int cnt = 0;
+        for (int i = beg; i < end; i++) cnt += mark[i] != kNone;
+        int total;
+        int r = block_exclusive_scan<NT>(cnt, S.wsum, &total);
+        for (int i = beg; i < end; i++)
+            if (mark[i] != kNone) R.fin_rank[mark[i]] = r++;
+    }
+    __syncthreads();
+    uint8_t* len = G.len + (int64_t)off / 3 + e;
+    for (int k = tid; k < T; k += NT) len[R.fin_rank[k]] = (uint8_t)(R.finals[k] >> 16);
+    __syncthreads();
+    int H;
+    {
+        const int chunk = (T + NT - 1) / NT;
+        const int beg = min(T, tid * chunk), end = min(T, beg + chunk);
+        int cnt = 0;
+        for (int r = beg; r < end; r++) cnt += len[r];
+        int st = block_exclusive_scan<NT>(cnt, S.wsum, &H);
+        for (int r = beg; r < end; r++) {
+            R.fin_start[r] = st;
+            st += len[r];
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < T; k += NT) {
+        uint32_t v = R.finals[k];
+        int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
+        int st = R.fin_start[R.fin_rank[k]];
+        for (int j = nh - 1; j >= 0; j--) {
+            G.hits[(int64_t)off + st + j] = off + __float_as_int(R.coords[q].w);
+            q = R.prev[q];
+        }
+    }
+    if (tid == 0) {
+        G.ev_ntracks[e] = T;
+        G.ev_nhits[e] = H;
+        out.event_status[e] = SBT_OK;
+    }
+}
+
+__device__ __forceinline__ void fail_event(int e, int code, const Staging& G, const sbt_tracks& out)
+{
+    if (threadIdx.x == 0) {
+        G.ev_ntracks[e] = 0;
+        G.ev_nhits[e] = 0;
+        out.event_status[e] = code;
+    }
+}
+
+template <int NT>
+__device__ void run_event(const DevConfig& C, const Inputs& in, const Work& W, const Staging& G,
+                          const sbt_tracks& out, int e, int64_t hb, int64_t r, int cap,
+                          const Smem& S)
+{
+    const int off = in.offsets[e];
+    const int n = in.offsets[e + 1] - off;
+    if (n < 0) {
+        fail_event(e, SBT_ERR_ARG, G, out);
+        return;
+    }
+    if (n > C.nmax || n > cap) {
+        fail_event(e, SBT_ERR_CAPACITY, G, out);
+        return;
+    }
+    Region R = region_of(W, hb, r, cap);
+    if (!sort_stage<NT>(C, in, off, n, R, S)) {
+        fail_event(e, SBT_ERR_ARG, G, out);
+        __syncthreads();
+        return;
+    }
+    if (!search_stage<NT>(C, R, S)) {
+        fail_event(e, SBT_ERR_CAPACITY, G, out);
+        __syncthreads();
+        return;
+    }
+    tracklet_filter<NT>(C, R, S);
+    output_stage<NT>(e, off, n, R, S, G, out);
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- kernels ---
+
+// One block per event.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_reco_plain(DevConfig C, Inputs in, Work W, Staging G,
+                                                    sbt_tracks out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S = carve(smem_raw, C.nmax, C.fcap, NT);
+    const int e = blockIdx.x;
+    const int off = in.offsets[e];
+    const int n = in.offsets[e + 1] - off;
+    run_event<NT>(C, in, W, G, out, e, off, e, n, S);
+}
+
+// Persistent: each resident block takes events from the work queue in the
+// order of G.order (largest first) and reuses its own scratch region.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_reco_persistent(DevConfig C, Inputs in, Work W, Staging G,
+                                                         sbt_tracks out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S = carve(smem_raw, C.nmax, C.fcap, NT);
+    const int64_t hb = (int64_t)blockIdx.x * C.nmax;
+    for (;;) {
+        if (threadIdx.x == 0) S.misc[kEvent] = atomicAdd(&G.queue[0], 1);
+        __syncthreads();
+        const int q = S.misc[kEvent];
+        __syncthreads();
+        if (q >= in.n_events) break;
+        run_event<NT>(C, in, W, G, out, G.order[q], hb, blockIdx.x, C.nmax, S);
+    }
+}
+
+// Processing order, largest events first (counting sort on size classes).
+__global__ void __launch_bounds__(1024) k_order(Inputs in, Staging G)
+{
+    __shared__ int hist[1024];
+    __shared__ int wsum[33];
+    const int tid = threadIdx.x;
+    const int E = in.n_events;
+    hist[tid] = 0;
+    __syncthreads();
+    for (int e = tid; e < E; e += 1024) {
+        int n = in.offsets[e + 1] - in.offsets[e];
+        int b = 1023 - min(max(n, 0) >> 4, 1023);
+        atomicAdd(&hist[b], 1);
+    }
+    __syncthreads();
+    int v = hist[tid];
+    int total;
+    int ex = block_exclusive_scan<1024>(v, wsum, &total);
+    hist[tid] = ex;
+    __syncthreads();
+    for (int e = tid; e < E; e += 1024) {
+        int n = in.offsets[e + 1] - in.offsets[e];
+        int b = 1023 - min(max(n, 0) >> 4, 1023);
+        G.order[atomicAdd(&hist[b], 1)] = e;
+    }
+}
+
+// Device-wide exclusive scan of the per-event track and hit counts, with the
+// capacity check.  One block; each thread owns a contiguous run of events.
+__global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks out)
+{
+    __shared__ int wsum[33];
+    const int tid = threadIdx.x;
+    const int E = in.n_events;
+    const int chunk = (E + 1023) / 1024;
+    const int beg = min(E, tid * chunk), end = min(E, beg + chunk);
+    int t = 0, h = 0, f = 0;
+    for (int e = beg; e < end; e++) {
+        t += G.ev_ntracks[e];
+        h += G.ev_nhits[e];
+        f += out.event_status[e] != SBT_OK;
+    }
+    int T, H, F;
+    int bt = block_exclusive_scan<1024>(t, wsum, &T);
+    int bh = block_exclusive_scan<1024>(h, wsum, &H);
+    block_exclusive_scan<1024>(f, wsum, &F);
+    for (int e = beg; e < end; e++) {
+        G.track_base[e] = bt;
+        G.hit_base[e] = bh;
+        out.track_offsets[e] = bt;
+        bt += G.ev_ntracks[e];
+        bh += G.ev_nhits[e];
+    }
+    if (tid == 0) {
+        out.track_offsets[E] = T;
+        bool ok = T <= out.cap_tracks && H <= out.cap_hits;
+        if (ok) out.hit_offsets[T] = H;
+        out.counts[0] = T;
+        out.counts[1] = H;
+        out.counts[2] = ok ? SBT_OK : SBT_ERR_CAPACITY;
+        out.counts[3] = F;
+    }
+}
+
+// Consolidation: one warp per event; each lane copies one track's hits into
+// the CSR output and fits it.
+__global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Staging G,
+                                                      sbt_tracks out)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= in.n_events) return;
+    const int e = warp;
+    const int off = in.offsets[e];
+    const int T = G.ev_ntracks[e];
+    const int tb = G.track_base[e], hbse = G.hit_base[e];
+    const uint8_t* len = G.len + (int64_t)off / 3 + e;
+    int carry = 0;
+    for (int r0 = 0; r0 < T; r0 += 32) {
+        int r = r0 + lane;
+        int l = r < T ? len[r] : 0;
+        int incl = l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int start = carry + incl - l;
+        carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (r >= T) continue;
+        int g = tb + r;
+        int ho = hbse + start;
+        if (g >= out.cap_tracks || (int64_t)ho + l > out.cap_hits) continue;
+        out.hit_offsets[g] = ho;
+        const int32_t* src = G.hits + (int64_t)off + start;
+        for (int j = 0; j < l; j++) out.track_hits[ho + j] = src[j];
+        float p[4], chi2;
+        fit_line(
+            l,
+            [&](int i) {
+                int h = src[i];
+                return make_float3(in.x[h], in.y[h], in.z[h]);
+            },
+            C.sigma, p, &chi2);
+        out.params[4 * (int64_t)g + 0] = p[0];
+        out.params[4 * (int64_t)g + 1] = p[1];
+        out.params[4 * (int64_t)g + 2] = p[2];
+        out.params[4 * (int64_t)g + 3] = p[3];
+        out.chi2[g] = chi2;
+        out.ndof[g] = 2 * l - 4;
+    }
+}
+
+// Sort stage alone, for stage-level checks.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_debug_sort(DevConfig C, Inputs in, Work W, uint16_t* phi16,
+                                                    int32_t* perm, int32_t* modoff, int32_t* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S = carve(smem_raw, C.nmax, C.fcap, NT);
+    const int e = blockIdx.x;
+    const int off = in.offsets[e];
+    const int n = in.offsets[e + 1] - off;
+    if (n < 0 || n > C.nmax) {
+        if (threadIdx.x == 0) status[e] = SBT_ERR_CAPACITY;
+        return;
+    }
+    Region R = region_of(W, off, e, n);
+    if (!sort_stage<NT>(C, in, off, n, R, S)) {
+        if (threadIdx.x == 0) status[e] = SBT_ERR_ARG;
+        return;
+    }
+    for (int p = threadIdx.x; p < n; p += NT) {
+        phi16[off + p] = S.phi[p];
+        perm[off + p] = __float_as_int(R.coords[p].w);
+    }
+    for (int m = threadIdx.x; m <= C.M; m += NT) modoff[(int64_t)e * (C.M + 1) + m] = S.modoff[m];
+    if (threadIdx.x == 0) status[e] = SBT_OK;
+}
+
+__global__ void k_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint16_t)phi16_of(x[i], y[i]);
+}
+
+// ------------------------------------------------------------ launchers ---
+
+template <int NT>
+static cudaError_t plain_nt(const DevConfig& C, const Inputs& in, const Work& W, const Staging& G,
+                            const sbt_tracks& out, cudaStream_t st)
+{
+    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    cudaError_t err = cudaFuncSetAttribute(k_reco_plain<NT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (in.n_events > 0) k_reco_plain<NT><<<in.n_events, NT, sm, st>>>(C, in, W, G, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Work& W, const Staging& S,
+                         const sbt_tracks& out, int threads, cudaStream_t stream)
+{
+    switch (threads) {
+        case 64: return plain_nt<64>(C, in, W, S, out, stream);
+        case 128: return plain_nt<128>(C, in, W, S, out, stream);
+        case 256: return plain_nt<256>(C, in, W, S, out, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream)
+{
+    k_order<<<1, 1024, 0, stream>>>(in, S);
+    return cudaGetLastError();
+}
+
+template <int NT>
+static int occupancy_nt(const DevConfig& C)
+{
+    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    if (cudaFuncSetAttribute(k_reco_persistent<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess)
+        return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_reco_persistent<NT>, NT, sm) !=
+        cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+int persistent_blocks_per_sm(const DevConfig& C, int threads)
+{
+    switch (threads) {
+        case 64: return occupancy_nt<64>(C);
+        case 128: return occupancy_nt<128>(C);
+        case 256: return occupancy_nt<256>(C);
+        default: return 0;
+    }
+}
+
+template <int NT>
+static cudaError_t persistent_nt(const DevConfig& C, const Inputs& in, const Work& W,
+                                 const Staging& G, const sbt_tracks& out, int blocks,
+                                 cudaStream_t st)
+{
+    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    cudaError_t err = cudaFuncSetAttribute(k_reco_persistent<NT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (blocks > 0) k_reco_persistent<NT><<<blocks, NT, sm, st>>>(C, in, W, G, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Work& W,
+                              const Staging& S, const sbt_tracks& out, int threads, int blocks,
+                              cudaStream_t stream)
+{
+    switch (threads) {
+        case 64: return persistent_nt<64>(C, in, W, S, out, blocks, stream);
+        case 128: return persistent_nt<128>(C, in, W, S, out, blocks, stream);
+        case 256: return persistent_nt<256>(C, in, W, S, out, blocks, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_scan(const Inputs& in, const Staging& S, const sbt_tracks& out,
+                        cudaStream_t stream)
+{
+    k_scan<<<1, 1024, 0, stream>>>(in, S, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_consolidate(const DevConfig& C, const Inputs& in, const Staging& S,
+                               const sbt_tracks& out, cudaStream_t stream)
+{
+    if (in.n_events > 0) {
+        int blocks = (in.n_events + 7) / 8;
+        k_consolidate<<<blocks, 256, 0, stream>>>(C, in, S, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const DevConfig& C, const Inputs& in, const Staging& S,
+                          const sbt_tracks& out, cudaStream_t stream)
+{
+    cudaError_t e = launch_scan(in, S, out, stream);
+    if (e == cudaSuccess) e = launch_consolidate(C, in, S, out, stream);
+    return e;
+}
+
+int plain_kernel_count() { return 3; }
+
+template <int NT>
+static cudaError_t debug_sort_nt(const DevConfig& C, const Inputs& in, const Work& W, uint16_t* phi16,
+                                 int32_t* perm, int32_t* modoff, int32_t* status, cudaStream_t st)
+{
+    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    cudaError_t err = cudaFuncSetAttribute(k_debug_sort<NT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (in.n_events > 0)
+        k_debug_sort<NT><<<in.n_events, NT, sm, st>>>(C, in, W, phi16, perm, modoff, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_sort(const DevConfig& C, const Inputs& in, const Work& W,
+                              uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
+                              int32_t* status, int threads, cudaStream_t stream)
+{
+    switch (threads) {
+        case 64: return debug_sort_nt<64>(C, in, W, phi16, perm, module_offsets, status, stream);
+        case 128: return debug_sort_nt<128>(C, in, W, phi16, perm, module_offsets, status, stream);
+        case 256: return debug_sort_nt<256>(C, in, W, phi16, perm, module_offsets, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out,
+                               cudaStream_t stream)
+{
+    if (n > 0) k_debug_phi16<<<(n + 255) / 256, 256, 0, stream>>>(x, y, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sbt

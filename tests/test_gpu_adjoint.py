@@ -1,0 +1,97 @@
+"""GPU adjoint of the alignment objective against the fp64 oracle and central
+differences, and its torch.autograd wrapper."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_03936_gb300 import synth
+from tests.test_oracle_alignment import truth_tracks
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SIGMA = 0.012
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2207_03936_gb300 import sbt
+    ev = synth.make_events(5, 40, workers=1)
+    ho, th = truth_tracks(ev)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(hit_sigma=SIGMA))
+    d = {k: torch.from_numpy(v).cuda() for k, v in
+         dict(x=ev.x, y=ev.y, z=ev.z, m=ev.module, ho=ho, th=th).items()}
+    yield sbt, h, ev, ho, th, d
+    h.close()
+
+
+def test_adjoint_matches_oracle_gradient(setup):
+    sbt, h, ev, ho, th, d = setup
+    rng = np.random.default_rng(8)
+    align = np.concatenate([rng.normal(0, 0.005, (52, 3)), rng.normal(0, 5e-5, (52, 3))], 1)
+    c, g = sbt.sbt_fit_adjoint(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"],
+                               torch.from_numpy(align).cuda())
+    torch.cuda.synchronize()
+    v, go = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, align, SIGMA)
+    assert abs(float(c.item()) - v) <= 1e-12 * v
+    g = g.cpu().numpy()
+    scale = np.abs(go).max()
+    assert (np.abs(g - go) <= 1e-9 * np.maximum(np.abs(go), 1e-3 * scale)).all()
+
+
+def test_adjoint_against_central_differences(setup):
+    sbt, h, ev, ho, th, d = setup
+    rng = np.random.default_rng(9)
+    align = np.concatenate([rng.normal(0, 0.005, (52, 3)), rng.normal(0, 5e-5, (52, 3))], 1)
+    a = torch.from_numpy(align).cuda()
+    _, g = sbt.sbt_fit_adjoint(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"], a)
+    g = g.cpu().numpy()
+    fd = np.zeros_like(g)
+    for m in range(52):
+        for k in range(6):
+            step = 1e-4 if k < 3 else 1e-5
+            ap = align.copy(); ap[m, k] += step
+            am = align.copy(); am[m, k] -= step
+            fp, _ = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, ap, SIGMA, False)
+            fm, _ = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, am, SIGMA, False)
+            fd[m, k] = (fp - fm) / (2 * step)
+    scale = np.abs(fd).max()
+    assert (np.abs(g - fd) <= 1e-6 * np.maximum(np.abs(fd), 1e-3 * scale)).all()
+
+
+def test_adjoint_is_bitwise_reproducible(setup):
+    sbt, h, ev, ho, th, d = setup
+    a = torch.zeros(52, 6, dtype=torch.float64, device="cuda")
+    c1, g1 = sbt.sbt_fit_adjoint(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"], a)
+    c2, g2 = sbt.sbt_fit_adjoint(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"], a)
+    assert torch.equal(c1, c2) and torch.equal(g1, g2)
+
+
+def test_autograd_function(setup):
+    sbt, h, ev, ho, th, d = setup
+    a = torch.zeros(52, 6, dtype=torch.float64, device="cuda", requires_grad=True)
+    loss = sbt.alignment_chi2(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"], a)
+    (2.0 * loss).backward()
+    _, g = sbt.sbt_fit_adjoint(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"], a.detach())
+    assert torch.allclose(a.grad, 2.0 * g, rtol=0, atol=0)
+    # a gradient step lowers the objective
+    with torch.no_grad():
+        step = -1e-9 * a.grad
+        l2 = sbt.alignment_chi2(h, d["x"], d["y"], d["z"], d["m"], d["ho"], d["th"], a + step)
+    assert float(l2) < float(loss)
+
+
+def test_adjoint_on_reconstructed_tracks(setup):
+    sbt, h, ev, ho, th, d = setup
+    out = sbt.sbt_reconstruct_batched(h, d["x"], d["y"], d["z"], d["m"],
+                                      torch.from_numpy(ev.event_offsets).cuda())
+    r = out.compact()
+    a = np.zeros((52, 6))
+    c, g = sbt.sbt_fit_adjoint(h, d["x"], d["y"], d["z"], d["m"],
+                               torch.from_numpy(r["hit_offsets"]).cuda(),
+                               torch.from_numpy(r["track_hits"]).cuda(), torch.from_numpy(a).cuda())
+    v, go = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, r["hit_offsets"], r["track_hits"],
+                              ev.module_z, a, SIGMA)
+    assert abs(float(c.item()) - v) <= 1e-12 * v
+    # the fp64 objective at zero alignment equals the sum of the fp32 fits
+    assert abs(v - float(r["chi2"].astype(np.float64).sum())) <= 1e-3 * v

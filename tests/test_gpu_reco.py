@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Track sets, hit lists, fitted parameters and chi2 must be bit-identical to the
+oracle's (fp32 decision arithmetic, every operation rounded as written on
+both sides); the stated tolerance for the fit parameters (1e-5 relative) is
+therefore met with margin zero.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_03936_gb300 import synth
+from tests.hand_events import MZ, assemble, line_hits, single_track
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CFG = dict(k_doublets=4, max_scatter_seed=0.04, max_scatter_follow=0.04, max_chi2_tracklet=20.0,
+           hit_sigma=0.012)
+
+
+@pytest.fixture(scope="module")
+def sbt():
+    from paper_2207_03936_gb300 import sbt as s
+    s.lib()
+    return s
+
+
+@pytest.fixture(scope="module")
+def handle(sbt):
+    h = sbt.sbt_create(MZ, sbt.default_config(**CFG))
+    yield h
+    h.close()
+
+
+def to_dev(ev):
+    d = "cuda"
+    return (torch.from_numpy(ev.x).to(d), torch.from_numpy(ev.y).to(d), torch.from_numpy(ev.z).to(d),
+            torch.from_numpy(ev.module).to(d), torch.from_numpy(ev.event_offsets).to(d))
+
+
+def arrays(x, y, z, m):
+    off = np.array([0, len(x)], np.int32)
+    return synth.Events(np.asarray(x, np.float32), np.asarray(y, np.float32),
+                        np.asarray(z, np.float32), np.asarray(m, np.int32), off,
+                        np.full(len(x), -1, np.int32), 0, MZ)
+
+
+def run_gpu(sbt, handle, ev, batched=False):
+    fn = sbt.sbt_reconstruct_batched if batched else sbt.sbt_reconstruct
+    out = fn(handle, *to_dev(ev))
+    torch.cuda.synchronize()
+    return out.compact()
+
+
+def assert_same(g, o):
+    assert (g["event_status"] == o.status).all()
+    assert int(g["counts"][2]) == 0
+    assert np.array_equal(g["track_offsets"], o.track_offsets)
+    assert np.array_equal(g["hit_offsets"], o.hit_offsets)
+    assert np.array_equal(g["track_hits"], o.track_hits)
+    assert np.array_equal(g["ndof"], o.ndof)
+    # bit-identical fits (the contract is 1e-5 relative)
+    assert np.array_equal(g["params"].view(np.uint32), o.params.view(np.uint32))
+    assert np.array_equal(g["chi2"].view(np.uint32), o.chi2.view(np.uint32))
+
+
+def oracle_of(ev):
+    return oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                              oracle.config(**CFG))
+
+
+def test_phi16_bit_exact(sbt):
+    rng = np.random.default_rng(0)
+    ang = np.linspace(-np.pi, np.pi, 200001)
+    r = rng.uniform(0.01, 60.0, ang.shape[0])
+    x = np.concatenate([r * np.cos(ang), rng.uniform(-50, 50, 100000), [0.0, -1.0, 1.0, 0.0, -3.0]])
+    y = np.concatenate([r * np.sin(ang), rng.uniform(-50, 50, 100000), [0.0, 0.0, 0.0, 2.0, -0.0]])
+    x, y = x.astype(np.float32), y.astype(np.float32)
+    g = sbt.sbt_debug_phi16(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(g.cpu().numpy().view(np.uint16), oracle.phi16(x, y))
+
+
+def test_sort_stage_bit_exact(sbt, handle):
+    ev = synth.make_events(2, 60, workers=1)
+    phi, perm, mo = sbt.sbt_debug_sort(handle, *[to_dev(ev)[i] for i in (0, 1, 3, 4)])
+    torch.cuda.synchronize()
+    phi = phi.cpu().numpy().view(np.uint16)
+    perm = perm.cpu().numpy()
+    mo = mo.cpu().numpy()
+    for e in range(ev.n_events):
+        lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+        p, o, ph = oracle.sort_event(ev.x[lo:hi], ev.y[lo:hi], ev.module[lo:hi], 52)
+        assert np.array_equal(perm[lo:hi], p)
+        assert np.array_equal(phi[lo:hi], ph)
+        assert np.array_equal(mo[e], o)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_small_workload_bit_exact(sbt, handle, batched):
+    ev = synth.make_events(1, workers=1)
+    assert_same(run_gpu(sbt, handle, ev, batched), oracle_of(ev))
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_upgrade_workload_bit_exact(sbt, handle, batched):
+    ev = synth.make_events(2)
+    assert_same(run_gpu(sbt, handle, ev, batched), oracle_of(ev))
+
+
+def test_uneven_workload_bit_exact(sbt, handle):
+    ev = synth.make_events(3, 400)
+    o = oracle_of(ev)
+    assert_same(run_gpu(sbt, handle, ev, False), o)
+    assert_same(run_gpu(sbt, handle, ev, True), o)
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_block_sizes_agree(sbt, threads):
+    ev = synth.make_events(2, 120, workers=1)
+    h = sbt.sbt_create(MZ, sbt.default_config(threads_per_block=threads, **CFG))
+    try:
+        o = oracle_of(ev)
+        assert_same(run_gpu(sbt, h, ev, False), o)
+        assert_same(run_gpu(sbt, h, ev, True), o)
+    finally:
+        h.close()
+
+
+def test_hand_built_events(sbt, handle):
+    cases = []
+    x, y, z, m, _ = single_track()
+    cases.append((x, y, z, m))
+    x, y, z, m, _ = single_track(missing=(20, 21))
+    cases.append((x, y, z, m))
+    t = np.array([0.003, 0.02])
+    zc = float(MZ[11])
+    mods = [k for k in range(0, 24) if k != 11]
+    A = line_hits(12.0 - t[0] * zc, -t[1] * zc, t[0], t[1], mods)
+    B = (A[0].copy(), -A[1], A[2].copy(), A[3].copy())
+    S = (np.array([12.05], np.float32), np.array([0.0], np.float32), np.array([MZ[11]], np.float32),
+         np.array([11], np.int32))
+    x, y, z, m, _ = assemble([A, B, S], shuffle_seed=9)
+    cases.append((x, y, z, m))
+    jit = np.where(np.arange(20) % 2 == 0, 0.003, -0.003)
+    cases.append(line_hits(9.0, 0.0, 0.002, 0.0, range(5, 25), jitter=(np.zeros(20), jit)))
+    xs, ys, zs, ms, offs = [], [], [], [], [0]
+    for (x, y, z, m) in cases:
+        xs.append(x); ys.append(y); zs.append(z); ms.append(m); offs.append(offs[-1] + len(x))
+    ev = synth.Events(np.concatenate(xs), np.concatenate(ys), np.concatenate(zs),
+                      np.concatenate(ms).astype(np.int32), np.array(offs, np.int32),
+                      np.zeros(offs[-1], np.int32), 0, MZ)
+    o = oracle_of(ev)
+    assert_same(run_gpu(sbt, handle, ev, False), o)
+    assert_same(run_gpu(sbt, handle, ev, True), o)
+
+
+def test_edge_cases_empty_and_degenerate(sbt, handle):
+    # empty batch
+    ev = synth.Events(*(np.zeros(0, np.float32),) * 3, np.zeros(0, np.int32), np.zeros(1, np.int32),
+                      np.zeros(0, np.int32), 0, MZ)
+    for b in (False, True):
+        g = run_gpu(sbt, handle, ev, b)
+        assert g["counts"][0] == 0 and g["counts"][1] == 0
+    # zero-hit events between real ones, and hits on one module only
+    base = synth.make_events(2, 5, workers=1)
+    lo, hi = base.event_offsets[1], base.event_offsets[2]
+    one_mod = np.full(7, 3, np.int32)
+    x = np.concatenate([base.x[lo:hi], np.linspace(6, 9, 7, dtype=np.float32)])
+    y = np.concatenate([base.y[lo:hi], np.linspace(6, 9, 7, dtype=np.float32)])
+    z = np.concatenate([base.z[lo:hi], np.full(7, MZ[3], np.float32)])
+    m = np.concatenate([base.module[lo:hi], one_mod])
+    n1 = hi - lo
+    offs = np.array([0, 0, n1, n1, n1 + 7, n1 + 7], np.int32)
+    ev = synth.Events(x, y, z, m, offs, np.zeros(len(x), np.int32), 0, MZ)
+    o = oracle_of(ev)
+    for b in (False, True):
+        assert_same(run_gpu(sbt, handle, ev, b), o)
+
+
+def test_bad_module_and_oversize_events_are_reported(sbt):
+    ev = synth.make_events(2, 6, workers=1)
+    m = ev.module.copy()
+    lo = ev.event_offsets[2]
+    m[lo + 3] = 52                      # event 2: module id out of range
+    sizes = np.diff(ev.event_offsets)
+    big = int(np.argmax(sizes))
+    h = sbt.sbt_create(MZ, sbt.default_config(max_hits_per_event=int(sizes[big]) - 1, **CFG))
+    try:
+        bad = synth.Events(ev.x, ev.y, ev.z, m, ev.event_offsets, ev.mc, 0, MZ)
+        for b in (False, True):
+            g = run_gpu(sbt, h, bad, b)
+            st = g["event_status"]
+            assert st[2] == sbt.SBT_ERR_ARG
+            if big != 2:
+                assert st[big] == sbt.SBT_ERR_CAPACITY
+            assert g["counts"][3] == (st != 0).sum()
+            # the other events are untouched
+            ok = [e for e in range(ev.n_events) if st[e] == 0]
+            for e in ok:
+                lo_, hi_ = ev.event_offsets[e], ev.event_offsets[e + 1]
+                one = oracle.event(ev.x[lo_:hi_], ev.y[lo_:hi_], ev.z[lo_:hi_], m[lo_:hi_], MZ,
+                                   oracle.config(**CFG))
+                t0, t1 = g["track_offsets"][e], g["track_offsets"][e + 1]
+                assert t1 - t0 == one.n_tracks
+                hs = g["track_hits"][g["hit_offsets"][t0]:g["hit_offsets"][t1]] - lo_
+                assert np.array_equal(hs, one.track_hits)
+            for e in range(ev.n_events):
+                if st[e] != 0:
+                    assert g["track_offsets"][e] == g["track_offsets"][e + 1]
+    finally:
+        h.close()
+
+
+def test_output_capacity_overflow_is_reported(sbt, handle):
+    ev = synth.make_events(2, 10, workers=1)
+    x, y, z, m, off = to_dev(ev)
+    o = oracle_of(ev)
+    out = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, cap_tracks=o.n_tracks - 1)
+    sbt.sbt_reconstruct(handle, x, y, z, m, off, out=out)
+    torch.cuda.synchronize()
+    c = out.counts.cpu().numpy()
+    assert c[2] == sbt.SBT_ERR_CAPACITY and c[0] == o.n_tracks and c[1] == len(o.track_hits)
+
+
+def test_repeat_runs_are_identical(sbt, handle):
+    ev = synth.make_events(2, 200, workers=1)
+    a = run_gpu(sbt, handle, ev, True)
+    b = run_gpu(sbt, handle, ev, True)
+    c = run_gpu(sbt, handle, ev, False)
+    for k in a:
+        assert np.array_equal(a[k], b[k]) and np.array_equal(a[k], c[k])
+
+
+def test_host_entry_point_matches_device(sbt, handle):
+    ev = synth.make_events(2, 150, workers=1)
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    out = sbt.sbt_reconstruct_host(handle, pin(ev.x), pin(ev.y), pin(ev.z), pin(ev.module),
+                                   pin(ev.event_offsets))
+    T, H = int(out.counts[0]), int(out.counts[1])
+    o = oracle_of(ev)
+    assert T == o.n_tracks and H == len(o.track_hits)
+    assert np.array_equal(out.track_offsets.numpy(), o.track_offsets)
+    assert np.array_equal(out.hit_offsets[:T + 1].numpy(), o.hit_offsets)
+    assert np.array_equal(out.track_hits[:H].numpy(), o.track_hits)
+    assert np.array_equal(out.params[:4 * T].numpy().reshape(T, 4), o.params)
+
+
+def test_autotune_keeps_results(sbt):
+    ev = synth.make_events(2, 300, workers=1)
+    h = sbt.sbt_create(MZ, sbt.default_config(**CFG))
+    try:
+        chosen = sbt.sbt_autotune(h, *to_dev(ev))
+        assert chosen in (64, 128, 256)
+        assert_same(run_gpu(sbt, h, ev, True), oracle_of(ev))
+    finally:
+        h.close()
