@@ -152,7 +152,8 @@ sbt_status check_inputs(sbt_handle* h, const float* x, const float* y, const flo
     if (!offsets) return fail(h, SBT_ERR_ARG, "event_offsets is NULL");
     if (n_hits > 0 && (!x || !y || !z || !module)) return fail(h, SBT_ERR_ARG, "hit array is NULL");
     if (out) {
-        if (!out->track_offsets || !out->hit_offsets || !out->event_status || !out->counts)
+        if (!out->track_offsets || !out->hit_offsets || !out->counts ||
+            (n_events > 0 && !out->event_status))
             return fail(h, SBT_ERR_ARG, "output array is NULL");
         if (out->cap_tracks < 0 || out->cap_hits < 0) return fail(h, SBT_ERR_ARG, "negative capacity");
         if ((out->cap_tracks > 0 && (!out->params || !out->chi2 || !out->ndof)) ||

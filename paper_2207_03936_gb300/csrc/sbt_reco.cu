@@ -171,6 +171,13 @@ struct Plan {
     size_t phi, flag, modoff, forming, misc, tot, base, wsum, total;
 };
 
+// Bytes of the forming-track buffers: 9 uint16 arrays, one float array and
+// 4 uint8 arrays of fcap entries, each starting on a 16-byte boundary.
+__host__ __device__ inline size_t forming_bytes(int fcap)
+{
+    return 9 * align16(2 * (size_t)fcap) + align16(4 * (size_t)fcap) + 4 * align16((size_t)fcap);
+}
+
 __host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
 {
     Plan p;
@@ -178,7 +185,7 @@ __host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
     p.phi = o;      o = align16(o + 2 * (size_t)nmax);
     p.flag = o;     o = align16(o + (size_t)nmax);
     p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
-    size_t form = 26 * (size_t)fcap;
+    size_t form = forming_bytes(fcap);
     size_t hist = 4 * 256 * (size_t)(threads / 32);
     p.forming = o;  o = align16(o + (form > hist ? form : hist));
     p.misc = o;     o = align16(o + 4 * kMiscN);
@@ -199,24 +206,26 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int fcap, int threads
     S.flag = raw + p.flag;
     S.modoff = (int*)(raw + p.modoff);
     unsigned char* f = raw + p.forming;
+    const size_t a16 = align16(2 * (size_t)fcap), a32 = align16(4 * (size_t)fcap),
+                 a8 = align16((size_t)fcap);
     for (int b = 0; b < 2; b++)
         for (int k = 0; k < 3; k++) {
             S.fh[b][k] = (uint16_t*)f;
-            f += 2 * (size_t)fcap;
+            f += a16;
         }
     for (int b = 0; b < 2; b++) {
         S.fkey[b] = (uint16_t*)f;
-        f += 2 * (size_t)fcap;
+        f += a16;
     }
     S.fcand = (uint16_t*)f;
-    f += 2 * (size_t)fcap;
+    f += a16;
     S.fsc = (float*)f;
-    f += 4 * (size_t)fcap;
+    f += a32;
     for (int b = 0; b < 2; b++) {
         S.fnh[b] = f;
-        f += fcap;
+        f += a8;
         S.fsk[b] = f;
-        f += fcap;
+        f += a8;
     }
     S.hist = (int*)(raw + p.forming);
     S.misc = (int*)(raw + p.misc);

@@ -33,6 +33,22 @@ def aligned_events():
     return ev, ho, th
 
 
+def central_differences(fun, align):
+    """Fourth-order central differences (h^4 truncation), per parameter."""
+    fd = np.zeros_like(align)
+    for m in range(align.shape[0]):
+        for k in range(6):
+            h = 1e-4 if k < 3 else 1e-5
+
+            def at(d):
+                a = align.copy()
+                a[m, k] += d
+                return fun(a)
+
+            fd[m, k] = (-at(2 * h) + 8 * at(h) - 8 * at(-h) + at(-2 * h)) / (12 * h)
+    return fd
+
+
 def f(ev, ho, th, align):
     return oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, align, SIGMA,
                              want_grad=False)[0]
@@ -44,13 +60,7 @@ def test_gradient_matches_central_differences(aligned_events):
     align = np.concatenate([rng.normal(0, 0.005, (52, 3)), rng.normal(0, 5e-5, (52, 3))], 1)
     v, g = oracle.align_chi2(ev.x, ev.y, ev.z, ev.module, ho, th, ev.module_z, align, SIGMA)
     assert abs(v - f(ev, ho, th, align)) == 0.0
-    fd = np.zeros_like(g)
-    for m in range(52):
-        for k in range(6):
-            h = 1e-4 if k < 3 else 1e-5
-            ap = align.copy(); ap[m, k] += h
-            am = align.copy(); am[m, k] -= h
-            fd[m, k] = (f(ev, ho, th, ap) - f(ev, ho, th, am)) / (2 * h)
+    fd = central_differences(lambda a: f(ev, ho, th, a), align)
     scale = np.abs(fd).max()
     err = np.abs(g - fd)
     assert (err <= 1e-6 * np.maximum(np.abs(fd), 1e-3 * scale)).all(), err.max()
