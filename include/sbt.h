@@ -204,6 +204,31 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
                                int32_t n_events, int32_t n_hits, const sbt_tracks* out, int32_t reps,
                                float* ms, void* stream);
 
+/*
+ * Reconstruction for callers that cannot allocate device memory: for example
+ * a trigger or serving process that reserves all its device memory at start-up
+ * and forbids allocation afterwards (cudaMalloc and cudaFree synchronise the
+ * device and can fail once the memory is taken), or a plug-in inside an
+ * application that owns the device memory pool.  The paper has no
+ * counterpart; it computes exactly what sbt_reconstruct computes.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
+ *     workspace is a fixed array of about 26 MB inside the library's device
+ *     image, held by every GPU that loads the library until the process exits.
+ *   - At most 524288 hits and 32768 events per call; larger batches return
+ *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).
+ *   - The first call on each device looks up the workspace address on that
+ *     device; make that first call before any stream capture.
+ *   - Every call on a device shares the one workspace: calls whose work
+ *     overlaps on the GPU (other streams, other handles, other threads) race
+ *     and corrupt each other's results; serialise them.
+ * Arguments, layouts and results are those of sbt_reconstruct; sbt_create
+ * allocates no device memory, so a handle can be made by such callers too.
+ */
+sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, const float* y, const float* z,
+                                   const int32_t* module, const int32_t* event_offsets,
+                                   int32_t n_events, int32_t n_hits, const sbt_tracks* out,
+                                   void* stream);
+
 /* Number of kernels the last reconstruction call on h enqueued (launch
  * accounting for benchmarks); 0 before any call. */
 int32_t sbt_last_launch_count(const sbt_handle* h);

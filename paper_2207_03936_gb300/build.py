@@ -22,6 +22,7 @@ UNITS = {
     "sbt_adjoint.cu": [],
     "sbt_api.cu": [],
     "sbt_server.cu": [],
+    "sbt_noalloc.cu": [],
 }
 
 

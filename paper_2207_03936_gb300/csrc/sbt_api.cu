@@ -217,6 +217,16 @@ sbt_status enqueue_batched(sbt_handle* h, const Inputs& in, const Staging& S, co
 
 }  // namespace
 
+namespace sbt {
+
+const DevConfig& handle_device_config(const sbt_handle* h) { return h->C; }
+
+int handle_plain_threads(const sbt_handle* h) { return default_threads(h, false); }
+
+void handle_set_error(sbt_handle* h, const std::string& msg) { h->err = msg; }
+
+}  // namespace sbt
+
 extern "C" {
 
 sbt_status sbt_default_config(sbt_config* out)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "sbt.h"
@@ -98,5 +99,10 @@ cudaError_t launch_adjoint(const DevConfig& C, const Inputs& in, const int32_t* 
                            double* chi2_sum, double* grad, const AdjointWork& W,
                            cudaStream_t stream);
 int adjoint_blocks();
+
+// Handle accessors for translation units that cannot see the handle type.
+const DevConfig& handle_device_config(const sbt_handle* h);
+int handle_plain_threads(const sbt_handle* h);
+void handle_set_error(sbt_handle* h, const std::string& msg);
 
 }  // namespace sbt

@@ -252,6 +252,19 @@ def sbt_reconstruct_host(h: Handle, x, y, z, module, event_offsets, out: TrackOu
     return out
 
 
+def sbt_reconstruct_noalloc(h: Handle, x, y, z, module, event_offsets, out: TrackOutput,
+                            stream=None) -> TrackOutput:
+    """sbt_reconstruct for callers that must not allocate device memory: the
+    library allocates nothing (its workspace is a fixed array in its device
+    image, at most 524288 hits and 32768 events per call) and the caller passes
+    preallocated outputs.  Calls that overlap on the GPU share that workspace
+    and must be serialised."""
+    f = lib().sbt_reconstruct_noalloc
+    f.restype = _I32
+    f.argtypes = [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]
+    return _reco(f, h, x, y, z, module, event_offsets, out, stream)
+
+
 def sbt_autotune(h: Handle, x, y, z, module, event_offsets, stream=None) -> int:
     px, py, pz, pm, po, E, H = _inputs(x, y, z, module, event_offsets)
     chosen = ctypes.c_int32()
@@ -328,3 +341,4 @@ class AlignmentChi2(torch.autograd.Function):
 
 def alignment_chi2(handle: Handle, x, y, z, module, hit_offsets, track_hits, align):
     return AlignmentChi2.apply(align, handle, x, y, z, module, hit_offsets, track_hits)
+
