@@ -29,6 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2207_03936_gb300 import synth  # noqa: E402  (numpy only; no CUDA)
+
 METRIC = "VELO events/s on 1 GB300, batched vs plain; p99 latency; track-set match"
 WORKLOAD = "uneven batch: 100k events, pileup U(1,20), Poisson(25)+10% backward tracks per vertex"
 
@@ -43,6 +45,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-sweep", action="store_true",
+                   help="sweep arrival rate (0.1-1.5x of saturation) and memory budget (2-16 GB)")
     return p.parse_args()
 
 
@@ -114,6 +119,34 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def serve(sbt, h, ev, rate_hz, budget_bytes, streams=4, max_batch=512, timeout=120.0):
+    """Open-loop Poisson arrivals at rate_hz into the request loop; returns
+    events/s (completions over the span from first arrival to last
+    completion) and submit-to-done latency percentiles."""
+    srv = sbt.Server(h, budget_bytes, streams, max_batch)
+    try:
+        if rate_hz is None:
+            arrival = np.zeros(ev.n_events)
+        else:
+            arrival = synth.poisson_arrivals(rate_hz, ev.n_events, seed=11)
+        t0 = time.perf_counter()
+        srv.submit_schedule(ev, arrival)
+        lat = []
+        while len(lat) < ev.n_events and time.perf_counter() - t0 < timeout:
+            for r in srv.poll(4096, timeout_s=0.01):
+                lat.append(r.latency_s)
+        span = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    lat = np.array(lat)
+    return {"offered_hz": rate_hz, "events": int(len(lat)), "value": len(lat) / span,
+            "unit": "events/s", "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+            "budget_gb": budget_bytes / 2**30, "mean_batch_events": st["mean_batch_events"],
+            "peak_inflight_gb": st["peak_bytes"] / 2**30}
+
+
 def cpu_baseline(ev, budget_s: float, gpu_out=None):
     """The oracle on all host cores over a bounded sample of the workload's
     events; optionally compares its tracks with the GPU's for those events."""
@@ -156,7 +189,6 @@ def cpu_baseline(ev, budget_s: float, gpu_out=None):
 
 
 def run_reference(args, ws, rank):
-    from paper_2207_03936_gb300 import synth
     if rank != 0:
         return
     ev = synth.make_events(3, args.events)
@@ -181,13 +213,13 @@ def run_reference(args, ws, rank):
 def main():
     args = parse()
     ws, rank, local = dist_env()
-    from paper_2207_03936_gb300 import synth
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
     # inputs are drawn before any CUDA call (the generator uses spawned workers)
     ev = synth.make_events(3, args.events, seed=rank)
     ev_adj = None if args.no_adjoint else synth.make_events(5)
+    ev_srv = None if args.no_serving else synth.make_events(4, 40_000, seed=7)
 
     import torch
     from paper_2207_03936_gb300 import sbt
@@ -297,6 +329,16 @@ def main():
         ams = a.elapsed_time(b) / args.steps
         adj = {"value": ev_adj.n_events / (ams / 1e3), "unit": "events/s", "ms_per_step": ams,
                "events": ev_adj.n_events, "tracks": int(rc["counts"][0]), "dtype": "f64"}
+    serving = None
+    if ev_srv is not None:
+        sat = serve(sbt, h, ev_srv, None, 4 << 30)          # all events at once: saturation
+        rates = [0.5, 0.9] if not args.serving_sweep else [0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.3, 1.5]
+        budgets = [4 << 30] if not args.serving_sweep else [2 << 30, 4 << 30, 8 << 30, 16 << 30]
+        runs = [serve(sbt, h, ev_srv, f * sat["value"], b) for b in budgets for f in rates]
+        serving = {"workload": "upgrade-condition events, open-loop Poisson arrivals",
+                   "saturation": sat, "runs": runs,
+                   "p99_ms_at_0.9x": next((r["p99_ms"] for r in runs
+                                          if abs(r["offered_hz"] - 0.9 * sat["value"]) < 1e-6), None)}
     h.close()
 
     if rank == 0:
@@ -310,6 +352,7 @@ def main():
                        "tracks": T, "threads_per_block": threads,
                        "l2": "inputs larger than L2 (no flush needed)"},
             "plain": plain,
+            "serving": serving,
             "match": match,
             "adjoint": adj,
             "e2e": e2e,

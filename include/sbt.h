@@ -269,6 +269,15 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
 sbt_status sbt_server_submit(sbt_server* s, int64_t request_id, const float* x, const float* y,
                              const float* z, const int32_t* module, int32_t n);
 
+/* Open-loop load generator: a native thread submits event e of the host batch
+ * (x, y, z, module [event_offsets[e] .. event_offsets[e+1])) arrival_s[e]
+ * seconds after this call, with request id first_id + e.  The call copies the
+ * batch and returns at once; results arrive through sbt_server_poll. */
+sbt_status sbt_server_submit_schedule(sbt_server* s, const float* x, const float* y,
+                                      const float* z, const int32_t* module,
+                                      const int32_t* event_offsets, int32_t n_events,
+                                      const double* arrival_s, int64_t first_id);
+
 /* Up to max_results finished requests into results[] (host); *n_out receives
  * the count.  Waits at most timeout_s for the first one (0 = do not wait);
  * returns SBT_ERR_TIMEOUT when none finished in time. */

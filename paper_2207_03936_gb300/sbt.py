@@ -342,3 +342,105 @@ class AlignmentChi2(torch.autograd.Function):
 def alignment_chi2(handle: Handle, x, y, z, module, hit_offsets, track_hits, align):
     return AlignmentChi2.apply(align, handle, x, y, z, module, hit_offsets, track_hits)
 
+
+# ------------------------------------------------------------------ serving --
+
+
+def _server_sigs():
+    L = lib()
+    sig = {
+        "sbt_server_create": (_I32, [_P, _I64, _I32, _I32, _P]),
+        "sbt_server_submit": (_I32, [_P, _I64, _P, _P, _P, _P, _I32]),
+        "sbt_server_submit_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _P, _I64]),
+        "sbt_server_poll": (_I32, [_P, _P, _I32, _P, ctypes.c_double]),
+        "sbt_server_release": (_I32, [_P, _I64]),
+        "sbt_server_stats": (_I32, [_P, _P]),
+        "sbt_server_inject_failure": (_I32, [_P]),
+        "sbt_server_destroy": (_I32, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+@dataclasses.dataclass
+class ServedResult:
+    request_id: int
+    status: int
+    hit_offsets: "object"
+    track_hits: "object"
+    params: "object"
+    chi2: "object"
+    latency_s: float
+
+
+class Server:
+    """Continuous-batching request loop (sbt_server_* in include/sbt.h)."""
+
+    def __init__(self, handle: Handle, memory_budget_bytes: int, max_streams: int = 4,
+                 max_batch_events: int = 256):
+        self.L = _server_sigs()
+        s = ctypes.c_void_p()
+        _check(self.L.sbt_server_create(handle.h, int(memory_budget_bytes), int(max_streams),
+                                        int(max_batch_events), ctypes.byref(s)))
+        self.s = s
+        self._keep = []
+
+    def submit(self, request_id: int, x, y, z, module):
+        import numpy as np
+        x, y, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, z))
+        module = np.ascontiguousarray(module, dtype=np.int32)
+        _check(self.L.sbt_server_submit(self.s, int(request_id), x.ctypes.data, y.ctypes.data,
+                                        z.ctypes.data, module.ctypes.data, x.shape[0]))
+
+    def submit_schedule(self, ev, arrival_s, first_id: int = 0):
+        import numpy as np
+        arrays = [np.ascontiguousarray(a) for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+        at = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        _check(self.L.sbt_server_submit_schedule(self.s, *[a.ctypes.data for a in arrays],
+                                                 ev.n_events, at.ctypes.data, int(first_id)))
+
+    def poll(self, max_results: int = 1024, timeout_s: float = 0.0):
+        import numpy as np
+        buf = (ResultC * max_results)()
+        n = ctypes.c_int32()
+        st = self.L.sbt_server_poll(self.s, buf, max_results, ctypes.byref(n), float(timeout_s))
+        if st == SBT_ERR_TIMEOUT:
+            return []
+        _check(st)
+        out = []
+        for r in buf[:n.value]:
+            T = r.n_tracks
+            ho = np.ctypeslib.as_array((ctypes.c_int32 * (T + 1)).from_address(r.hit_offsets)).copy()
+            H = int(ho[-1])
+            th = (np.ctypeslib.as_array((ctypes.c_int32 * H).from_address(r.track_hits)).copy()
+                  if H else np.zeros(0, np.int32))
+            pr = (np.ctypeslib.as_array((ctypes.c_float * (4 * T)).from_address(r.params)).copy()
+                  if T else np.zeros(0, np.float32))
+            c2 = (np.ctypeslib.as_array((ctypes.c_float * T).from_address(r.chi2)).copy()
+                  if T else np.zeros(0, np.float32))
+            out.append(ServedResult(r.request_id, r.status, ho, th, pr.reshape(T, 4), c2, r.latency_s))
+            self.L.sbt_server_release(self.s, r.request_id)
+        return out
+
+    def stats(self) -> dict:
+        v = (ctypes.c_double * 8)()
+        _check(self.L.sbt_server_stats(self.s, v))
+        return {"completed": v[0], "submitted": v[1], "batches": v[2], "mean_batch_events": v[3],
+                "peak_bytes": v[4], "failed_batches": v[5]}
+
+    def inject_failure(self):
+        _check(self.L.sbt_server_inject_failure(self.s))
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.L.sbt_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

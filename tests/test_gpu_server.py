@@ -1,0 +1,78 @@
+"""Continuous-batching request loop: every served result equals the result of
+the same event reconstructed alone; events submitted while others run are
+admitted as slots and budget free up; a host-side batch failure completes its
+requests with an error and the loop continues."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_03936_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def collect(server, n, timeout=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < n and time.time() - t0 < timeout:
+        for r in server.poll(256, timeout_s=0.05):
+            got[r.request_id] = r
+    return got
+
+
+def test_served_results_equal_results_alone():
+    from paper_2207_03936_gb300 import sbt
+    ev = synth.make_events(2, 300, workers=1)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config())
+    srv = sbt.Server(h, memory_budget_bytes=64 << 20, max_streams=4, max_batch_events=32)
+    try:
+        arrival = synth.poisson_arrivals(20000.0, ev.n_events, seed=3)
+        srv.submit_schedule(ev, arrival)
+        got = collect(srv, ev.n_events)
+        st = srv.stats()
+    finally:
+        srv.close()
+        h.close()
+    assert len(got) == ev.n_events
+    assert st["batches"] > 1 and st["peak_bytes"] <= 64 << 20
+    for e in range(ev.n_events):
+        lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+        one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], ev.module_z)
+        r = got[e]
+        assert r.status == 0
+        assert np.array_equal(r.hit_offsets, one.hit_offsets)
+        assert np.array_equal(r.track_hits, one.track_hits)
+        assert np.array_equal(r.params, one.params)
+        assert r.latency_s > 0
+
+
+def test_overlapping_admission_and_failure_recovery():
+    from paper_2207_03936_gb300 import sbt
+    ev = synth.make_events(2, 120, workers=1)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config())
+    # a small budget forces several batches in flight and waiting admissions
+    srv = sbt.Server(h, memory_budget_bytes=8 << 20, max_streams=3, max_batch_events=8)
+    try:
+        srv.inject_failure()
+        for e in range(ev.n_events):
+            lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+            srv.submit(e, ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi])
+        got = collect(srv, ev.n_events)
+        st = srv.stats()
+    finally:
+        srv.close()
+        h.close()
+    assert len(got) == ev.n_events
+    failed = [r for r in got.values() if r.status == sbt.SBT_ERR_CUDA]
+    assert 1 <= len(failed) <= 8 and st["failed_batches"] == 1
+    assert st["batches"] >= ev.n_events / 8
+    ok = [r for r in got.values() if r.status == 0]
+    assert len(ok) == ev.n_events - len(failed)
+    for r in ok:
+        e = r.request_id
+        lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+        one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], ev.module_z)
+        assert np.array_equal(r.track_hits, one.track_hits)
