@@ -212,7 +212,7 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
  * application that owns the device memory pool.  The paper has no
  * counterpart; it computes exactly what sbt_reconstruct computes.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *     workspace is a fixed array of about 26 MB inside the library's device
+ *     workspace is a fixed array of about 30 MB inside the library's device
  *     image, held by every GPU that loads the library until the process exits.
  *   - At most 524288 hits and 32768 events per call; larger batches return
  *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).

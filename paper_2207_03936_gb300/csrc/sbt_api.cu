@@ -87,6 +87,8 @@ size_t carve_staging(void* base, int64_t n_hits, int64_t n_events, Staging* S)
     Staging s;
     s.hits = c.take<int32_t>(n_hits);
     s.len = c.take<uint8_t>(n_hits / 3 + n_events + 1);
+    s.fit = c.take<float4>(n_hits / 3 + n_events + 1);
+    s.chi2 = c.take<float>(n_hits / 3 + n_events + 1);
     s.ev_ntracks = c.take<int32_t>(n_events);
     s.ev_nhits = c.take<int32_t>(n_events);
     s.track_base = c.take<int32_t>(n_events);

@@ -54,6 +54,8 @@ struct Work {
 struct Staging {
     int32_t* hits;        // [n_hits]: event e writes from event_offsets[e]
     uint8_t* len;         // [n_hits / 3 + n_events + 1]: event e from off/3 + e
+    float4* fit;          // same indexing as len: (x0, y0, tx, ty) per track
+    float* chi2;          // same indexing as len
     int32_t* ev_ntracks;  // [n_events]
     int32_t* ev_nhits;    // [n_events]
     int32_t* track_base;  // [n_events]

@@ -29,7 +29,7 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // kNoAllocMaxHits hits and kNoAllocMaxEvents events), each 256-byte aligned.
 struct Layout {
     size_t coords, keys, idxA, idxB, prev, claim, tracklets, tl_q, finals, fin_rank, fin_start;
-    size_t hits, len, ntracks, nhits, track_base, hit_base, order, queue, total;
+    size_t hits, len, fit, chi2, ntracks, nhits, track_base, hit_base, order, queue, total;
 };
 
 constexpr Layout make_layout()
@@ -51,6 +51,8 @@ constexpr Layout make_layout()
     L.fin_start = o;  o = align256(o + 4 * (size_t)FN);
     L.hits = o;       o = align256(o + 4 * (size_t)H);
     L.len = o;        o = align256(o + (size_t)(H / 3 + E + 1));
+    L.fit = o;        o = align256(o + 16 * (size_t)(H / 3 + E + 1));
+    L.chi2 = o;       o = align256(o + 4 * (size_t)(H / 3 + E + 1));
     L.ntracks = o;    o = align256(o + 4 * (size_t)E);
     L.nhits = o;      o = align256(o + 4 * (size_t)E);
     L.track_base = o; o = align256(o + 4 * (size_t)E);
@@ -63,7 +65,7 @@ constexpr Layout make_layout()
 
 constexpr Layout kLayout = make_layout();
 
-// The workspace (about 26 MB).  In host code this name is only a host-side
+// The workspace (about 30 MB).  In host code this name is only a host-side
 // stand-in: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_workspace[kLayout.total];
 
@@ -141,6 +143,8 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     Staging S;
     S.hits = (int32_t*)(base + L.hits);
     S.len = (uint8_t*)(base + L.len);
+    S.fit = (float4*)(base + L.fit);
+    S.chi2 = (float*)(base + L.chi2);
     S.ev_ntracks = (int32_t*)(base + L.ntracks);
     S.ev_nhits = (int32_t*)(base + L.nhits);
     S.track_base = (int32_t*)(base + L.track_base);

@@ -146,23 +146,28 @@ __device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* par
 
 // ------------------------------------------------------- shared layout ---
 
-enum Misc { kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kTotH = 6, kMiscN = 32 };
+enum Misc { kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kMiscN = 32 };
 
+// Per-block shared memory.  Forming tracks live in two buffers of FC slots
+// each (index buf * FC + slot) so that no pointer array is indexed at run time.
 struct Smem {
-    uint16_t* phi;
-    uint8_t* flag;
+    uint16_t* phi;      // phi16 by sorted position
+    uint32_t* flag;     // one bit per sorted position
     int* modoff;
-    uint16_t* fh[2][3];
-    uint16_t* fkey[2];
-    uint8_t* fnh[2];
-    uint8_t* fsk[2];
-    uint16_t* fcand;
-    float* fsc;
-    int* hist;  // radix histograms, aliases the forming buffers
+    uint16_t* f0;       // third-last hit   [2 * FC]
+    uint16_t* f1;       // second-last hit  [2 * FC]
+    uint16_t* f2;       // last hit         [2 * FC]
+    uint16_t* fkey;     // track key        [2 * FC]
+    uint8_t* fnh;       // hits             [2 * FC]
+    uint8_t* fsk;       // consecutive misses [2 * FC]
+    uint16_t* fcand;    // candidate hit of this step [FC]
+    float* fsc;         // its scatter      [FC]
+    int* hist;          // radix histograms, aliases the forming buffers
     int* misc;
-    int* tot;   // [256]
-    int* base;  // [256]
-    int* wsum;  // [33]
+    int* tot;           // [256]
+    int* base;          // [256]
+    int* wsum;          // [33]
+    int FC;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -171,11 +176,13 @@ struct Plan {
     size_t phi, flag, modoff, forming, misc, tot, base, wsum, total;
 };
 
-// Bytes of the forming-track buffers: 9 uint16 arrays, one float array and
-// 4 uint8 arrays of fcap entries, each starting on a 16-byte boundary.
+__host__ __device__ inline int fc_of(int fcap) { return (fcap + 7) & ~7; }
+
+// Bytes of the forming-track buffers (every sub-array 16-byte aligned).
 __host__ __device__ inline size_t forming_bytes(int fcap)
 {
-    return 9 * align16(2 * (size_t)fcap) + align16(4 * (size_t)fcap) + 4 * align16((size_t)fcap);
+    const size_t FC = (size_t)fc_of(fcap);
+    return 4 * align16(2 * 2 * FC) + 2 * align16(2 * FC) + align16(2 * FC) + align16(4 * FC);
 }
 
 __host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
@@ -183,7 +190,7 @@ __host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
     Plan p;
     size_t o = 0;
     p.phi = o;      o = align16(o + 2 * (size_t)nmax);
-    p.flag = o;     o = align16(o + (size_t)nmax);
+    p.flag = o;     o = align16(o + 4 * (((size_t)nmax + 31) / 32));
     p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
     size_t form = forming_bytes(fcap);
     size_t hist = 4 * 256 * (size_t)(threads / 32);
@@ -202,31 +209,21 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int fcap, int threads
 {
     Plan p = make_plan(nmax, fcap, threads);
     Smem S;
+    const int FC = fc_of(fcap);
+    S.FC = FC;
     S.phi = (uint16_t*)(raw + p.phi);
-    S.flag = raw + p.flag;
+    S.flag = (uint32_t*)(raw + p.flag);
     S.modoff = (int*)(raw + p.modoff);
     unsigned char* f = raw + p.forming;
-    const size_t a16 = align16(2 * (size_t)fcap), a32 = align16(4 * (size_t)fcap),
-                 a8 = align16((size_t)fcap);
-    for (int b = 0; b < 2; b++)
-        for (int k = 0; k < 3; k++) {
-            S.fh[b][k] = (uint16_t*)f;
-            f += a16;
-        }
-    for (int b = 0; b < 2; b++) {
-        S.fkey[b] = (uint16_t*)f;
-        f += a16;
-    }
-    S.fcand = (uint16_t*)f;
-    f += a16;
+    const size_t two16 = align16(2 * 2 * (size_t)FC), two8 = align16(2 * (size_t)FC);
+    S.f0 = (uint16_t*)f;   f += two16;
+    S.f1 = (uint16_t*)f;   f += two16;
+    S.f2 = (uint16_t*)f;   f += two16;
+    S.fkey = (uint16_t*)f; f += two16;
+    S.fnh = f;             f += two8;
+    S.fsk = f;             f += two8;
+    S.fcand = (uint16_t*)f; f += align16(2 * (size_t)FC);
     S.fsc = (float*)f;
-    f += a32;
-    for (int b = 0; b < 2; b++) {
-        S.fnh[b] = f;
-        f += a8;
-        S.fsk[b] = f;
-        f += a8;
-    }
     S.hist = (int*)(raw + p.forming);
     S.misc = (int*)(raw + p.misc);
     S.tot = (int*)(raw + p.tot);
@@ -235,11 +232,14 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int fcap, int threads
     return S;
 }
 
+__device__ __forceinline__ bool flagged(const Smem& S, int p) { return (S.flag[p >> 5] >> (p & 31)) & 1u; }
+__device__ __forceinline__ void set_flag(const Smem& S, int p) { atomicOr(&S.flag[p >> 5], 1u << (p & 31)); }
+
 struct Region {
     float4* coords;
-    uint32_t* keys;
-    uint16_t* idxA;
-    uint16_t* idxB;
+    uint32_t* keys;     // sort keys; afterwards the seeding work list
+    uint16_t* idxA;     // radix buffer; afterwards canonical-order marks
+    uint16_t* idxB;     // radix buffer; afterwards track hit positions in order
     uint16_t* prev;
     unsigned long long* claim;
     unsigned long long* tracklets;
@@ -404,51 +404,70 @@ __device__ bool sort_stage(const DevConfig& C, const Inputs& in, int off, int n,
     for (int p = tid; p < n; p += NT) {
         int i = R.idxB[p];
         S.phi[p] = (uint16_t)(R.keys[i] & 0xFFFFu);
-        S.flag[p] = 0;
         R.coords[p] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
         R.claim[p] = ~0ull;
         R.idxA[p] = kNone;  // canonical-order marks
     }
+    for (int w = tid; w < (n + 31) / 32; w += NT) S.flag[w] = 0u;
     __syncthreads();
     return true;
 }
 
 // ------------------------------------------------------ seeding, following ---
 
+// phi16 of a window centre.  Only the window bounds use it, and they carry a
+// margin of 16 units, so a fast division is enough here.
+__device__ __forceinline__ uint32_t phi16_window(float x, float y)
+{
+    const float a1 = 0.9998660f, a3 = -0.3302995f, a5 = 0.1801410f;
+    const float a7 = -0.0851330f, a9 = 0.0208351f;
+    float ax = fabsf(x), ay = fabsf(y);
+    float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    float t2 = t * t;
+    float p = ((((a9 * t2 + a7) * t2 + a5) * t2 + a3) * t2 + a1) * t;
+    if (ay > ax) p = 1.5707963f - p;
+    if (x < 0.0f) p = 3.1415927f - p;
+    if (y < 0.0f) p = -p;
+    return (uint32_t)__float2int_rn(p * 10430.378f) & 0xFFFFu;
+}
+
 // Best unflagged hit on module [b0, b0 + nb) for the prediction (xp, yp)
-// with scatter < S.  Hits outside a phi window around the prediction cannot
-// pass the cut: a hit within sqrt(S) of the prediction differs from it in
-// angle by at most asin(sqrt(S) / r), bounded by tan(asin u) = sqrt(S / (r^2
-// - S)); the window adds 1/16 of that plus 16 phi16 units for the rounding
-// and arctangent error of both phi values.  Predictions near the axis scan
-// the whole module.  `better(sc, b)` orders candidates.
+// with scatter < cut.  Hits outside a phi window around the prediction cannot
+// pass the cut: a hit within d = sqrt(cut) of the prediction differs from it
+// in angle by at most asin(d / r) <= d / sqrt(r^2 - d^2); the half-width adds
+// 1/16 of that plus 16 phi16 units for the rounding and arctangent error of
+// both phi values and for the approximate arithmetic of the bound itself.
+// Predictions near the axis (r <= 2 d) scan the whole module.  The scatter
+// of every hit in the window is computed exactly (rounded operations), and
+// `better(sc, b)` orders candidates.
 template <class Better, class Take>
 __device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int b0, int nb, float xp,
-                                            float yp, float cut, Better better, Take take)
+                                            float yp, float cut, float sqrt_cut, Better better,
+                                            Take take)
 {
     if (nb <= 0) return;
-    float rp2 = __fadd_rn(__fmul_rn(xp, xp), __fmul_rn(yp, yp));
-    int lo_idx = 0, count = nb;
+    float rp2 = xp * xp + yp * yp;
+    int lo_idx = 0;
     uint32_t lo = 0, width = 0xFFFFu;
     bool windowed = false;
     if (rp2 < 1.0e30f && rp2 > 4.0f * cut) {
-        float u = sqrtf(cut / (rp2 - cut));
-        float wf = u * 10430.378f * 1.0625f;
+        float wf = sqrt_cut * rsqrtf(rp2 - cut) * (10430.378f * 1.0625f);
         if (wf < 16000.0f) {
-            int W = (int)wf + 16;
-            uint32_t php = phi16_of(xp, yp);
-            lo = (php - (uint32_t)W) & 0xFFFFu;
-            width = 2u * (uint32_t)W;
+            uint32_t W = (uint32_t)wf + 16u;
+            uint32_t php = phi16_window(xp, yp);
+            lo = (php - W) & 0xFFFFu;
+            width = 2u * W;
             lo_idx = lower_bound16(S.phi + b0, nb, lo);
             windowed = true;
         }
     }
-    for (int k = 0; k < count; k++) {
+    for (int k = 0; k < nb; k++) {
         int e = lo_idx + k;
         if (e >= nb) e -= nb;
         int b = b0 + e;
         if (windowed && (((uint32_t)S.phi[b] - lo) & 0xFFFFu) > width) break;
-        if (S.flag[b]) continue;
+        if (flagged(S, b)) continue;
         float sc = scatter_of(R.coords[b], xp, yp);
         if (sc < cut && better(sc, b)) take(sc, b);
     }
@@ -459,8 +478,8 @@ __device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int 
 // each extrapolated through c to module s+2, where the unflagged hit of
 // least scatter under the cut is sought; the kept triplet minimises
 // (scatter, position of a, position of b).
-__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int s, int c, int& oa,
-                         int& ob)
+__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int s, int c, float sqrt_cut,
+                         int& oa, int& ob)
 {
     const int o0 = S.modoff[s], no = S.modoff[s + 1] - o0;
     const int i0 = S.modoff[s + 2], ni = S.modoff[s + 3] - i0;
@@ -490,13 +509,13 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int
             dn--;
         }
         if (found >= C.K && d > dK) break;
-        if (S.flag[a]) continue;
+        if (flagged(S, a)) continue;
         found++;
         if (found == C.K) dK = d;
         float xp, yp;
         extrapolate(R.coords[a], Cc, zi, xp, yp);
         scan_window(
-            S, R, i0, ni, xp, yp, C.S_seed,
+            S, R, i0, ni, xp, yp, C.S_seed, sqrt_cut,
             [&](float sc, int b) {
                 return !have || sc < best_sc ||
                        (sc == best_sc && (a < best_a || (a == best_a && b < best_b)));
@@ -517,7 +536,7 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int
 
 // Following: best unflagged hit on module t for the track's last two hits.
 __device__ bool follow_best(const DevConfig& C, const Smem& S, const Region& R, int t, int h1, int h2,
-                            int& cand, float& csc)
+                            float sqrt_cut, int& cand, float& csc)
 {
     const int b0 = S.modoff[t], nb = S.modoff[t + 1] - b0;
     float xp, yp;
@@ -526,7 +545,7 @@ __device__ bool follow_best(const DevConfig& C, const Smem& S, const Region& R, 
     float best = 0.0f;
     int bb = 0;
     scan_window(
-        S, R, b0, nb, xp, yp, C.S_follow,
+        S, R, b0, nb, xp, yp, C.S_follow, sqrt_cut,
         [&](float sc, int b) { return !have || sc < best || (sc == best && b < bb); },
         [&](float sc, int b) {
             have = true;
@@ -560,6 +579,18 @@ __device__ __forceinline__ void add_tracklet(const Smem& S, const Region& R, int
         S.misc[kErr] = SBT_ERR_CAPACITY;
 }
 
+__device__ __forceinline__ void put_track(const Smem& S, int buf, int slot, int h0, int h1, int h2,
+                                          int key, int nh, int sk)
+{
+    const int i = buf * S.FC + slot;
+    S.f0[i] = (uint16_t)h0;
+    S.f1[i] = (uint16_t)h1;
+    S.f2[i] = (uint16_t)h2;
+    S.fkey[i] = (uint16_t)key;
+    S.fnh[i] = (uint8_t)nh;
+    S.fsk[i] = (uint8_t)sk;
+}
+
 // Iterative seeding and following.  Returns false (uniformly) on overflow.
 // Claims carry a tag (64 - t) << 48 above (scatter bits, track key), so a
 // claim of an earlier step always compares larger than one of the current
@@ -567,59 +598,73 @@ __device__ __forceinline__ void add_tracklet(const Smem& S, const Region& R, int
 template <int NT>
 __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int M = C.M;
+    const int FC = S.FC;
     int* misc = S.misc;
+    const float sq_seed = sqrtf(C.S_seed), sq_follow = sqrtf(C.S_follow);
+    uint32_t* list = R.keys;  // free after the sort
     if (tid == 0) {
         misc[kCnt0] = 0;
         misc[kCnt1] = 0;
         misc[kNFin] = 0;
         misc[kNTl] = 0;
         misc[kErr] = 0;
+        misc[kList] = 0;
     }
     __syncthreads();
     int cur = 0;
     for (int s = 0; s + 2 <= M - 1; ++s) {
         const int nxt = cur ^ 1;
-        if (tid == 0) misc[kCnt0 + nxt] = 0;
-        // seeding over modules (s, s+1, s+2)
+        // gather the unflagged middle hits of module s+1 into a work list
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
-        for (int c = c0 + tid; c < c1; c += NT) {
-            if (S.flag[c]) continue;
+        for (int base = c0 + (tid & ~31); base < c1; base += NT) {
+            const int c = base + lane;
+            const bool ok = c < c1 && !flagged(S, c);
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+            int pos = 0;
+            if (lane == 0 && m) pos = atomicAdd(&misc[kList], __popc(m));
+            pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+            if (ok) list[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
+        }
+        __syncthreads();
+        const int nl = misc[kList];
+        // seeding over modules (s, s+1, s+2)
+        for (int i = tid; i < nl; i += NT) {
+            const int c = (int)list[i];
             int a, b;
-            if (seed_for(C, S, R, s, c, a, b)) {
+            if (seed_for(C, S, R, s, c, sq_seed, a, b)) {
                 int slot = atomicAdd(&misc[kCnt0 + cur], 1);
-                if (slot < C.fcap) {
-                    S.fh[cur][0][slot] = (uint16_t)a;
-                    S.fh[cur][1][slot] = (uint16_t)c;
-                    S.fh[cur][2][slot] = (uint16_t)b;
-                    S.fkey[cur][slot] = (uint16_t)c;
-                    S.fnh[cur][slot] = 3;
-                    S.fsk[cur][slot] = 0;
-                } else {
+                if (slot < C.fcap)
+                    put_track(S, cur, slot, a, c, b, c, 3, 0);
+                else
                     misc[kErr] = SBT_ERR_CAPACITY;
-                }
             }
         }
         __syncthreads();
         if (misc[kErr]) return false;
         const int nf = misc[kCnt0 + cur];
+        if (tid == 0) {
+            misc[kCnt0 + nxt] = 0;
+            misc[kList] = 0;
+        }
         const int t = s + 3;
         if (t <= M - 1) {
             const unsigned long long tag = (unsigned long long)(64 - t) << 48;
             // following: candidates and claims
             for (int f = tid; f < nf; f += NT) {
-                const int nh = S.fnh[cur][f];
-                const int h0 = S.fh[cur][0][f], h1 = S.fh[cur][1][f], h2 = S.fh[cur][2][f];
+                const int i = cur * FC + f;
+                const int nh = S.fnh[i];
+                const int h0 = S.f0[i], h1 = S.f1[i], h2 = S.f2[i];
                 uint16_t cand = kNone;
                 float sc = 0.0f;
-                if (nh == 3 && (S.flag[h0] | S.flag[h1] | S.flag[h2])) {
+                if (nh == 3 && (flagged(S, h0) || flagged(S, h1) || flagged(S, h2))) {
                     cand = kDead;
                 } else {
                     int b;
-                    if (follow_best(C, S, R, t, h1, h2, b, sc)) {
+                    if (follow_best(C, S, R, t, h1, h2, sq_follow, b, sc)) {
                         cand = (uint16_t)b;
-                        unsigned long long k = claim_key(tag, sc, S.fkey[cur][f]);
+                        unsigned long long k = claim_key(tag, sc, S.fkey[i]);
                         atomicMin(&R.claim[b], k);
                         if (nh == 3) {
                             atomicMin(&R.claim[h0], k);
@@ -636,10 +681,11 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
             for (int f = tid; f < nf; f += NT) {
                 const uint16_t cand = S.fcand[f];
                 if (cand == kDead) continue;
-                const int nh = S.fnh[cur][f];
-                const int h0 = S.fh[cur][0][f], h1 = S.fh[cur][1][f], h2 = S.fh[cur][2][f];
-                const int key = S.fkey[cur][f];
-                int sk = S.fsk[cur][f];
+                const int i = cur * FC + f;
+                const int nh = S.fnh[i];
+                const int h0 = S.f0[i], h1 = S.f1[i], h2 = S.f2[i];
+                const int key = S.fkey[i];
+                int sk = S.fsk[i];
                 bool won = false;
                 if (cand != kNone) {
                     unsigned long long k = claim_key(tag, S.fsc[f], key);
@@ -649,23 +695,18 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
                               __ldcg(&R.claim[h2]) == k;
                 }
                 if (won) {
-                    S.flag[cand] = 1;
+                    set_flag(S, cand);
                     if (nh == 3) {
-                        S.flag[h0] = 1;
-                        S.flag[h1] = 1;
-                        S.flag[h2] = 1;
+                        set_flag(S, h0);
+                        set_flag(S, h1);
+                        set_flag(S, h2);
                         R.prev[h0] = kNone;
                         R.prev[h1] = (uint16_t)h0;
                         R.prev[h2] = (uint16_t)h1;
                     }
                     R.prev[cand] = (uint16_t)h2;
                     int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
-                    S.fh[nxt][0][slot] = (uint16_t)h1;
-                    S.fh[nxt][1][slot] = (uint16_t)h2;
-                    S.fh[nxt][2][slot] = cand;
-                    S.fkey[nxt][slot] = (uint16_t)key;
-                    S.fnh[nxt][slot] = (uint8_t)(nh + 1);
-                    S.fsk[nxt][slot] = 0;
+                    put_track(S, nxt, slot, h1, h2, cand, key, nh + 1, 0);
                 } else {
                     sk += 1;
                     if (sk >= 2) {
@@ -675,12 +716,7 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
                             add_tracklet(S, R, h0, h1, h2, key);
                     } else {
                         int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
-                        S.fh[nxt][0][slot] = (uint16_t)h0;
-                        S.fh[nxt][1][slot] = (uint16_t)h1;
-                        S.fh[nxt][2][slot] = (uint16_t)h2;
-                        S.fkey[nxt][slot] = (uint16_t)key;
-                        S.fnh[nxt][slot] = (uint8_t)nh;
-                        S.fsk[nxt][slot] = (uint8_t)sk;
+                        put_track(S, nxt, slot, h0, h1, h2, key, nh, sk);
                     }
                 }
             }
@@ -689,12 +725,12 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
         } else {
             // last iteration: every forming track is finished
             for (int f = tid; f < nf; f += NT) {
-                const int nh = S.fnh[cur][f];
-                const int h0 = S.fh[cur][0][f], h1 = S.fh[cur][1][f], h2 = S.fh[cur][2][f];
+                const int i = cur * FC + f;
+                const int nh = S.fnh[i];
                 if (nh >= 4)
-                    add_final(S, R, h2, nh);
+                    add_final(S, R, S.f2[i], nh);
                 else
-                    add_tracklet(S, R, h0, h1, h2, S.fkey[cur][f]);
+                    add_tracklet(S, R, S.f0[i], S.f1[i], S.f2[i], S.fkey[i]);
             }
             __syncthreads();
         }
@@ -714,7 +750,7 @@ __device__ void tracklet_filter(const DevConfig& C, const Region& R, const Smem&
         int h[3] = {(int)(v & 0xFFFF), (int)((v >> 16) & 0xFFFF), (int)((v >> 32) & 0xFFFF)};
         int key = (int)(v >> 48);
         uint32_t q = 0xFFFFFFFFu;
-        if (!S.flag[h[0]] && !S.flag[h[1]] && !S.flag[h[2]]) {
+        if (!flagged(S, h[0]) && !flagged(S, h[1]) && !flagged(S, h[2])) {
             float chi2;
             fit_line(
                 3,
@@ -750,14 +786,16 @@ __device__ void tracklet_filter(const DevConfig& C, const Region& R, const Smem&
     __syncthreads();
 }
 
-// Canonical order (smallest input hit index) and staging of the hit lists.
+// Canonical order (smallest input hit index), staging of the hit lists and
+// the least-squares fit of every track on the cached sorted coordinates.
 template <int NT>
-__device__ void output_stage(int e, int off, int n, const Region& R, const Smem& S,
-                             const Staging& G, const sbt_tracks& out)
+__device__ void output_stage(const DevConfig& C, int e, int off, int n, const Region& R,
+                             const Smem& S, const Staging& G, const sbt_tracks& out)
 {
     const int tid = threadIdx.x;
     const int T = S.misc[kNFin];
     uint16_t* mark = R.idxA;
+    uint16_t* pos = R.idxB;
     for (int k = tid; k < T; k += NT) {
         uint32_t v = R.finals[k];
         int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
@@ -782,7 +820,8 @@ __device__ void output_stage(int e, int off, int n, const Region& R, const Smem&
             if (mark[i] != kNone) R.fin_rank[mark[i]] = r++;
     }
     __syncthreads();
-    uint8_t* len = G.len + (int64_t)off / 3 + e;
+    const int64_t slot0 = (int64_t)off / 3 + e;
+    uint8_t* len = G.len + slot0;
     for (int k = tid; k < T; k += NT) len[R.fin_rank[k]] = (uint8_t)(R.finals[k] >> 16);
     __syncthreads();
     int H;
@@ -801,11 +840,23 @@ __device__ void output_stage(int e, int off, int n, const Region& R, const Smem&
     for (int k = tid; k < T; k += NT) {
         uint32_t v = R.finals[k];
         int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
-        int st = R.fin_start[R.fin_rank[k]];
+        const int r = R.fin_rank[k];
+        const int st = R.fin_start[r];
         for (int j = nh - 1; j >= 0; j--) {
             G.hits[(int64_t)off + st + j] = off + __float_as_int(R.coords[q].w);
+            pos[st + j] = (uint16_t)q;
             q = R.prev[q];
         }
+        float p[4], chi2;
+        fit_line(
+            nh,
+            [&](int i) {
+                float4 c = R.coords[pos[st + i]];
+                return make_float3(c.x, c.y, c.z);
+            },
+            C.sigma, p, &chi2);
+        G.fit[slot0 + r] = make_float4(p[0], p[1], p[2], p[3]);
+        G.chi2[slot0 + r] = chi2;
     }
     if (tid == 0) {
         G.ev_ntracks[e] = T;
@@ -850,7 +901,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Work& W, c
         return;
     }
     tracklet_filter<NT>(C, R, S);
-    output_stage<NT>(e, off, n, R, S, G, out);
+    output_stage<NT>(C, e, off, n, R, S, G, out);
     __syncthreads();
 }
 
@@ -952,8 +1003,8 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
     }
 }
 
-// Consolidation: one warp per event; each lane copies one track's hits into
-// the CSR output and fits it.
+// Consolidation: one warp per event copies the event's staged, already
+// ordered and fitted tracks into the CSR output (coalesced within the warp).
 __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Staging G,
                                                       sbt_tracks out)
 {
@@ -963,8 +1014,11 @@ __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Sta
     const int e = warp;
     const int off = in.offsets[e];
     const int T = G.ev_ntracks[e];
+    const int H = G.ev_nhits[e];
     const int tb = G.track_base[e], hbse = G.hit_base[e];
-    const uint8_t* len = G.len + (int64_t)off / 3 + e;
+    if ((int64_t)tb + T > out.cap_tracks || (int64_t)hbse + H > out.cap_hits) return;
+    const int64_t slot0 = (int64_t)off / 3 + e;
+    const uint8_t* len = G.len + slot0;
     int carry = 0;
     for (int r0 = 0; r0 < T; r0 += 32) {
         int r = r0 + lane;
@@ -978,27 +1032,19 @@ __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Sta
         int start = carry + incl - l;
         carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
         if (r >= T) continue;
-        int g = tb + r;
-        int ho = hbse + start;
-        if (g >= out.cap_tracks || (int64_t)ho + l > out.cap_hits) continue;
-        out.hit_offsets[g] = ho;
-        const int32_t* src = G.hits + (int64_t)off + start;
-        for (int j = 0; j < l; j++) out.track_hits[ho + j] = src[j];
-        float p[4], chi2;
-        fit_line(
-            l,
-            [&](int i) {
-                int h = src[i];
-                return make_float3(in.x[h], in.y[h], in.z[h]);
-            },
-            C.sigma, p, &chi2);
-        out.params[4 * (int64_t)g + 0] = p[0];
-        out.params[4 * (int64_t)g + 1] = p[1];
-        out.params[4 * (int64_t)g + 2] = p[2];
-        out.params[4 * (int64_t)g + 3] = p[3];
-        out.chi2[g] = chi2;
+        const int g = tb + r;
+        out.hit_offsets[g] = hbse + start;
+        float4 p = G.fit[slot0 + r];
+        out.params[4 * (int64_t)g + 0] = p.x;
+        out.params[4 * (int64_t)g + 1] = p.y;
+        out.params[4 * (int64_t)g + 2] = p.z;
+        out.params[4 * (int64_t)g + 3] = p.w;
+        out.chi2[g] = G.chi2[slot0 + r];
         out.ndof[g] = 2 * l - 4;
     }
+    const int32_t* src = G.hits + off;
+    int32_t* dst = out.track_hits + hbse;
+    for (int j = lane; j < H; j += 32) dst[j] = src[j];
 }
 
 // Sort stage alone, for stage-level checks.
