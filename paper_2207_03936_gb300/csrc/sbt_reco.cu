@@ -146,7 +146,7 @@ __device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* par
 
 // ------------------------------------------------------- shared layout ---
 
-enum Misc { kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kMiscN = 32 };
+enum Misc { kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kNOuter = 7, kMiscN = 32 };
 
 // Per-block shared memory.  Forming tracks live in two buffers of FC slots
 // each (index buf * FC + slot) so that no pointer array is indexed at run time.
@@ -237,7 +237,7 @@ __device__ __forceinline__ void set_flag(const Smem& S, int p) { atomicOr(&S.fla
 
 struct Region {
     float4* coords;
-    uint32_t* keys;     // sort keys; afterwards the seeding work list
+    uint32_t* keys;     // sort keys; afterwards the seeding work lists
     uint16_t* idxA;     // radix buffer; afterwards canonical-order marks
     uint16_t* idxB;     // radix buffer; afterwards track hit positions in order
     uint16_t* prev;
@@ -473,43 +473,58 @@ __device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int 
     }
 }
 
+// First index in keys[0, n) whose upper 16 bits are >= v.
+__device__ __forceinline__ int lower_bound_hi16(const uint32_t* keys, int n, uint32_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((keys[mid] >> 16) < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // Seeding for middle hit c on module s+1: the unflagged hits of module s
 // nearest to c in phi (all hits at the K-th smallest distance included),
 // each extrapolated through c to module s+2, where the unflagged hit of
 // least scatter under the cut is sought; the kept triplet minimises
-// (scatter, position of a, position of b).
-__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int s, int c, float sqrt_cut,
-                         int& oa, int& ob)
+// (scatter, position of a, position of b).  `outer` lists the unflagged hits
+// of module s in sorted order as (phi16 << 16 | position), `nu` of them, so
+// the nearest-first walk visits no flagged hit.
+__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int s, int c,
+                         const uint32_t* outer, int nu, float sqrt_cut, int& oa, int& ob)
 {
-    const int o0 = S.modoff[s], no = S.modoff[s + 1] - o0;
     const int i0 = S.modoff[s + 2], ni = S.modoff[s + 3] - i0;
-    if (no <= 0 || ni <= 0) return false;
+    if (nu <= 0 || ni <= 0) return false;
     const uint32_t phc = S.phi[c];
     const float4 Cc = R.coords[c];
     const float zi = C.module_z[s + 2];
-    const int j = lower_bound16(S.phi + o0, no, phc);
+    const int j = lower_bound_hi16(outer, nu, phc);
     int up = j, dn = j - 1;
     int found = 0, dK = INT_MAX;
     bool have = false;
     float best_sc = 0.0f;
     int best_a = 0, best_b = 0;
-    for (int visited = 0; visited < no; visited++) {
-        int iu = up >= no ? up - no : up;
-        int id = dn < 0 ? dn + no : dn;
-        int du = phi_dist(S.phi[o0 + iu], phc);
-        int dd = phi_dist(S.phi[o0 + id], phc);
+    for (int visited = 0; visited < nu; visited++) {
+        const int iu = up >= nu ? up - nu : up;
+        const int id = dn < 0 ? dn + nu : dn;
+        const uint32_t ku = outer[iu], kd = outer[id];
+        const int du = phi_dist(ku >> 16, phc);
+        const int dd = phi_dist(kd >> 16, phc);
         int a, d;
         if (du < dd || (du == dd && iu <= id)) {
-            a = o0 + iu;
+            a = (int)(ku & 0xFFFFu);
             d = du;
             up++;
         } else {
-            a = o0 + id;
+            a = (int)(kd & 0xFFFFu);
             d = dd;
             dn--;
         }
         if (found >= C.K && d > dK) break;
-        if (flagged(S, a)) continue;
         found++;
         if (found == C.K) dK = d;
         float xp, yp;
@@ -616,8 +631,10 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
     int cur = 0;
     for (int s = 0; s + 2 <= M - 1; ++s) {
         const int nxt = cur ^ 1;
-        // gather the unflagged middle hits of module s+1 into a work list
+        // work lists: the unflagged middle hits of module s+1 (any order), and
+        // the unflagged hits of module s in sorted order (one warp, ballots)
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
+        uint32_t* outer = list + (c1 - c0);
         for (int base = c0 + (tid & ~31); base < c1; base += NT) {
             const int c = base + lane;
             const bool ok = c < c1 && !flagged(S, c);
@@ -627,13 +644,28 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
             pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
             if (ok) list[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
         }
+        if ((tid >> 5) == NT / 32 - 1) {
+            const int o0 = S.modoff[s], o1 = S.modoff[s + 1];
+            int nu = 0;
+            for (int base = o0; base < o1; base += 32) {
+                const int a = base + lane;
+                const bool ok = a < o1 && !flagged(S, a);
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+                if (ok)
+                    outer[nu + __popc(m & ((1u << lane) - 1u))] =
+                        ((uint32_t)S.phi[a] << 16) | (uint32_t)a;
+                nu += __popc(m);
+            }
+            if (lane == 0) misc[kNOuter] = nu;
+        }
         __syncthreads();
         const int nl = misc[kList];
+        const int nu = misc[kNOuter];
         // seeding over modules (s, s+1, s+2)
         for (int i = tid; i < nl; i += NT) {
             const int c = (int)list[i];
             int a, b;
-            if (seed_for(C, S, R, s, c, sq_seed, a, b)) {
+            if (seed_for(C, S, R, s, c, outer, nu, sq_seed, a, b)) {
                 int slot = atomicAdd(&misc[kCnt0 + cur], 1);
                 if (slot < C.fcap)
                     put_track(S, cur, slot, a, c, b, c, 3, 0);
