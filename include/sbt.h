@@ -67,7 +67,7 @@ typedef struct {
     float max_chi2_tracklet;     /* tracklet filter chi2 cut; default 20 */
     float hit_sigma;             /* hit resolution for chi2, mm; default 0.012 */
     int32_t max_hits_per_event;  /* events with more hits get SBT_ERR_CAPACITY; default 16384, <= 65533 */
-    int32_t max_forming_tracks;  /* per-event forming-track buffer; 0 = max(256, max_hits/16) */
+    int32_t max_forming_tracks;  /* forming tracks alive per event: n_hits/12 + 64; a positive value lowers the bound */
     int32_t threads_per_block;   /* 64, 128 or 256; 0 = 128 (batched: autotuned value if any) */
 } sbt_config;
 
@@ -212,9 +212,9 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
  * application that owns the device memory pool.  The paper has no
  * counterpart; it computes exactly what sbt_reconstruct computes.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *     workspace is a fixed array of about 30 MB inside the library's device
+ *     workspace is a fixed array of about 38 MB inside the library's device
  *     image, held by every GPU that loads the library until the process exits.
- *   - At most 524288 hits and 32768 events per call; larger batches return
+ *   - At most 524288 hits and 4096 events per call; larger batches return
  *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).
  *   - The first call on each device looks up the workspace address on that
  *     device; make that first call before any stream capture.

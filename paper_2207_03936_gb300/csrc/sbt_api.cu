@@ -67,6 +67,8 @@ size_t carve_work(void* base, int64_t hits, int64_t regions, Work* W)
     Carver c(base);
     Work w;
     w.coords = c.take<float4>(hits);
+    w.phi = c.take<uint16_t>(hits);
+    w.ft = c.take<FTrack>(forming_entries(hits, regions));
     w.keys = c.take<uint32_t>(hits);
     w.idxA = c.take<uint16_t>(hits);
     w.idxB = c.take<uint16_t>(hits);
@@ -279,8 +281,7 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
     h->C.C3 = c.max_chi2_tracklet;
     h->C.sigma = c.hit_sigma;
     h->C.nmax = c.max_hits_per_event;
-    h->C.fcap = c.max_forming_tracks ? c.max_forming_tracks : std::max(256, c.max_hits_per_event / 16);
-    if (h->C.fcap > 65535) h->C.fcap = 65535;
+    h->C.fcap = c.max_forming_tracks;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
@@ -292,8 +293,8 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
         delete h;
         return SBT_ERR_CUDA;
     }
-    if (smem_bytes(h->C.nmax, h->C.fcap, 256) > (size_t)max_optin) {
-        g_create_error = "max_hits_per_event / max_forming_tracks exceed shared memory";
+    if (smem_bytes(h->C.nmax, 256) > (size_t)max_optin) {
+        g_create_error = "max_hits_per_event exceeds shared memory";
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         delete h;
         return SBT_ERR_ARG;

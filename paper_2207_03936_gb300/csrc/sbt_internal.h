@@ -19,7 +19,7 @@ struct DevConfig {
     int K;
     float S_seed, S_follow, C3, sigma;
     int nmax;  // max hits per event
-    int fcap;  // forming-track buffer entries
+    int fcap;  // upper bound on forming tracks per event (0: forming_capacity(n) only)
 };
 
 struct Inputs {
@@ -32,12 +32,30 @@ struct Inputs {
     int32_t n_hits;
 };
 
+// A forming track: its last three hits (sorted positions), key, hit count,
+// consecutive misses, and this step's candidate hit and scatter.
+struct __align__(16) FTrack {
+    uint16_t h0, h1, h2, key;
+    uint8_t nh, sk;
+    uint16_t cand;
+    float sc;
+};
+
+// Forming-track capacity of an event of n hits, and the slots a region of
+// capacity cap reserves (two buffers).
+__host__ __device__ inline int forming_capacity(int n) { return n / 12 + 64; }
+__host__ __device__ inline int64_t forming_base(int64_t hb, int64_t r) { return 2 * (hb / 12 + 72 * r); }
+inline int64_t forming_entries(int64_t hits, int64_t regions) { return 2 * (hits / 12 + 72 * regions) + 2; }
+
 // Per-region scratch (a region is an event in the plain launch, a resident
 // block in the persistent launch).  Region r with hit base hb and capacity
 // cap owns per-hit arrays [hb, hb + cap), tracklets from hb/4 + r (cap/4 + 1
-// entries) and final-track records from hb/3 + r (cap/3 + 1 entries).
+// entries), final-track records from hb/3 + r (cap/3 + 1 entries) and
+// forming-track slots from forming_base(hb, r) (2 (cap/12 + 72) entries).
 struct Work {
     float4* coords;              // sorted (x, y, z, input index as int bits)
+    uint16_t* phi;               // phi16 by sorted position
+    FTrack* ft;                  // forming tracks, two buffers
     uint32_t* keys;              // (module << 16 | phi16) by input index
     uint16_t* idxA;              // radix ping buffer; canonical-order marks afterwards
     uint16_t* idxB;              // radix pong buffer; final sorted order
@@ -68,7 +86,7 @@ struct Staging {
 inline int64_t tracklet_entries(int64_t hits, int64_t regions) { return hits / 4 + regions + 1; }
 inline int64_t final_entries(int64_t hits, int64_t regions) { return hits / 3 + regions + 1; }
 
-size_t smem_bytes(int nmax, int fcap, int threads);
+size_t smem_bytes(int nmax, int threads);
 
 // Launchers (sbt_reco.cu).  All asynchronous on `stream`.
 cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Work& W, const Staging& S,

@@ -21,14 +21,14 @@ namespace {
 
 // Limits of one call: the workspace is sized for these.
 constexpr int64_t kNoAllocMaxHits = int64_t(1) << 19;   // 524288 hits
-constexpr int64_t kNoAllocMaxEvents = int64_t(1) << 15; // 32768 events
+constexpr int64_t kNoAllocMaxEvents = int64_t(1) << 12; // 4096 events
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Offsets of the workspace arrays (the Work and Staging layouts for
 // kNoAllocMaxHits hits and kNoAllocMaxEvents events), each 256-byte aligned.
 struct Layout {
-    size_t coords, keys, idxA, idxB, prev, claim, tracklets, tl_q, finals, fin_rank, fin_start;
+    size_t coords, phi, ft, keys, idxA, idxB, prev, claim, tracklets, tl_q, finals, fin_rank, fin_start;
     size_t hits, len, fit, chi2, ntracks, nhits, track_base, hit_base, order, queue, total;
 };
 
@@ -39,6 +39,8 @@ constexpr Layout make_layout()
     const int64_t TL = H / 4 + E + 1, FN = H / 3 + E + 1;
     size_t o = 0;
     L.coords = o;     o = align256(o + 16 * (size_t)H);
+    L.phi = o;        o = align256(o + 2 * (size_t)H);
+    L.ft = o;         o = align256(o + 16 * (size_t)(2 * (H / 12 + 72 * E) + 2));
     L.keys = o;       o = align256(o + 4 * (size_t)H);
     L.idxA = o;       o = align256(o + 2 * (size_t)H);
     L.idxB = o;       o = align256(o + 2 * (size_t)H);
@@ -65,7 +67,7 @@ constexpr Layout make_layout()
 
 constexpr Layout kLayout = make_layout();
 
-// The workspace (about 30 MB).  In host code this name is only a host-side
+// The workspace (about 38 MB).  In host code this name is only a host-side
 // stand-in: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_workspace[kLayout.total];
 
@@ -130,6 +132,8 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     const Layout& L = kLayout;
     Work W;
     W.coords = (float4*)(base + L.coords);
+    W.phi = (uint16_t*)(base + L.phi);
+    W.ft = (FTrack*)(base + L.ft);
     W.keys = (uint32_t*)(base + L.keys);
     W.idxA = (uint16_t*)(base + L.idxA);
     W.idxB = (uint16_t*)(base + L.idxB);

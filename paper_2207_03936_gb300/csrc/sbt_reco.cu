@@ -146,55 +146,38 @@ __device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* par
 
 // ------------------------------------------------------- shared layout ---
 
-enum Misc { kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kNOuter = 7, kMiscN = 32 };
+enum Misc {
+    kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kNOuter = 7,
+    kNew = 8, kMiscN = 32
+};
 
-// Per-block shared memory.  Forming tracks live in two buffers of FC slots
-// each (index buf * FC + slot) so that no pointer array is indexed at run time.
+// Per-block shared memory: flag bits, module offsets, radix histograms and
+// counters.  Everything sized by the event's hit count lives in the block's
+// global scratch region (L1-resident), so a block needs only a few KB and
+// many events are in flight per SM.
 struct Smem {
-    uint16_t* phi;      // phi16 by sorted position
     uint32_t* flag;     // one bit per sorted position
     int* modoff;
-    uint16_t* f0;       // third-last hit   [2 * FC]
-    uint16_t* f1;       // second-last hit  [2 * FC]
-    uint16_t* f2;       // last hit         [2 * FC]
-    uint16_t* fkey;     // track key        [2 * FC]
-    uint8_t* fnh;       // hits             [2 * FC]
-    uint8_t* fsk;       // consecutive misses [2 * FC]
-    uint16_t* fcand;    // candidate hit of this step [FC]
-    float* fsc;         // its scatter      [FC]
-    int* hist;          // radix histograms, aliases the forming buffers
+    int* hist;          // radix histograms [warps][256]
     int* misc;
     int* tot;           // [256]
     int* base;          // [256]
     int* wsum;          // [33]
-    int FC;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct Plan {
-    size_t phi, flag, modoff, forming, misc, tot, base, wsum, total;
+    size_t flag, modoff, hist, misc, tot, base, wsum, total;
 };
 
-__host__ __device__ inline int fc_of(int fcap) { return (fcap + 7) & ~7; }
-
-// Bytes of the forming-track buffers (every sub-array 16-byte aligned).
-__host__ __device__ inline size_t forming_bytes(int fcap)
-{
-    const size_t FC = (size_t)fc_of(fcap);
-    return 4 * align16(2 * 2 * FC) + 2 * align16(2 * FC) + align16(2 * FC) + align16(4 * FC);
-}
-
-__host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
+__host__ __device__ inline Plan make_plan(int nmax, int threads)
 {
     Plan p;
     size_t o = 0;
-    p.phi = o;      o = align16(o + 2 * (size_t)nmax);
     p.flag = o;     o = align16(o + 4 * (((size_t)nmax + 31) / 32));
     p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
-    size_t form = forming_bytes(fcap);
-    size_t hist = 4 * 256 * (size_t)(threads / 32);
-    p.forming = o;  o = align16(o + (form > hist ? form : hist));
+    p.hist = o;     o = align16(o + 4 * 256 * (size_t)(threads / 32));
     p.misc = o;     o = align16(o + 4 * kMiscN);
     p.tot = o;      o = align16(o + 4 * 256);
     p.base = o;     o = align16(o + 4 * 256);
@@ -203,28 +186,15 @@ __host__ __device__ inline Plan make_plan(int nmax, int fcap, int threads)
     return p;
 }
 
-size_t smem_bytes(int nmax, int fcap, int threads) { return make_plan(nmax, fcap, threads).total; }
+size_t smem_bytes(int nmax, int threads) { return make_plan(nmax, threads).total; }
 
-__device__ inline Smem carve(unsigned char* raw, int nmax, int fcap, int threads)
+__device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
 {
-    Plan p = make_plan(nmax, fcap, threads);
+    Plan p = make_plan(nmax, threads);
     Smem S;
-    const int FC = fc_of(fcap);
-    S.FC = FC;
-    S.phi = (uint16_t*)(raw + p.phi);
     S.flag = (uint32_t*)(raw + p.flag);
     S.modoff = (int*)(raw + p.modoff);
-    unsigned char* f = raw + p.forming;
-    const size_t two16 = align16(2 * 2 * (size_t)FC), two8 = align16(2 * (size_t)FC);
-    S.f0 = (uint16_t*)f;   f += two16;
-    S.f1 = (uint16_t*)f;   f += two16;
-    S.f2 = (uint16_t*)f;   f += two16;
-    S.fkey = (uint16_t*)f; f += two16;
-    S.fnh = f;             f += two8;
-    S.fsk = f;             f += two8;
-    S.fcand = (uint16_t*)f; f += align16(2 * (size_t)FC);
-    S.fsc = (float*)f;
-    S.hist = (int*)(raw + p.forming);
+    S.hist = (int*)(raw + p.hist);
     S.misc = (int*)(raw + p.misc);
     S.tot = (int*)(raw + p.tot);
     S.base = (int*)(raw + p.base);
@@ -237,6 +207,7 @@ __device__ __forceinline__ void set_flag(const Smem& S, int p) { atomicOr(&S.fla
 
 struct Region {
     float4* coords;
+    uint16_t* phi;
     uint32_t* keys;     // sort keys; afterwards the seeding work lists
     uint16_t* idxA;     // radix buffer; afterwards canonical-order marks
     uint16_t* idxB;     // radix buffer; afterwards track hit positions in order
@@ -248,12 +219,15 @@ struct Region {
     uint32_t* finals;
     int32_t* fin_rank;
     int32_t* fin_start;
+    FTrack* ft;         // buffer b starts at ft + b * fstride
+    int fstride;
 };
 
 __device__ inline Region region_of(const Work& W, int64_t hb, int64_t r, int cap)
 {
     Region R;
     R.coords = W.coords + hb;
+    R.phi = W.phi + hb;
     R.keys = W.keys + hb;
     R.idxA = W.idxA + hb;
     R.idxB = W.idxB + hb;
@@ -265,6 +239,8 @@ __device__ inline Region region_of(const Work& W, int64_t hb, int64_t r, int cap
     R.finals = W.finals + hb / 3 + r;
     R.fin_rank = W.fin_rank + hb / 3 + r;
     R.fin_start = W.fin_start + hb / 3 + r;
+    R.ft = W.ft + forming_base(hb, r);
+    R.fstride = cap / 12 + 72;
     return R;
 }
 
@@ -403,7 +379,7 @@ __device__ bool sort_stage(const DevConfig& C, const Inputs& in, int off, int n,
     radix_pass<NT>(R.keys, R.idxA, R.idxB, n, 16, 6, S, S.modoff, C.M);
     for (int p = tid; p < n; p += NT) {
         int i = R.idxB[p];
-        S.phi[p] = (uint16_t)(R.keys[i] & 0xFFFFu);
+        R.phi[p] = (uint16_t)(R.keys[i] & 0xFFFFu);
         R.coords[p] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
         R.claim[p] = ~0ull;
         R.idxA[p] = kNone;  // canonical-order marks
@@ -458,7 +434,7 @@ __device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int 
             uint32_t php = phi16_window(xp, yp);
             lo = (php - W) & 0xFFFFu;
             width = 2u * W;
-            lo_idx = lower_bound16(S.phi + b0, nb, lo);
+            lo_idx = lower_bound16(R.phi + b0, nb, lo);
             windowed = true;
         }
     }
@@ -466,7 +442,7 @@ __device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int 
         int e = lo_idx + k;
         if (e >= nb) e -= nb;
         int b = b0 + e;
-        if (windowed && (((uint32_t)S.phi[b] - lo) & 0xFFFFu) > width) break;
+        if (windowed && (((uint32_t)R.phi[b] - lo) & 0xFFFFu) > width) break;
         if (flagged(S, b)) continue;
         float sc = scatter_of(R.coords[b], xp, yp);
         if (sc < cut && better(sc, b)) take(sc, b);
@@ -499,7 +475,7 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int
 {
     const int i0 = S.modoff[s + 2], ni = S.modoff[s + 3] - i0;
     if (nu <= 0 || ni <= 0) return false;
-    const uint32_t phc = S.phi[c];
+    const uint32_t phc = R.phi[c];
     const float4 Cc = R.coords[c];
     const float zi = C.module_z[s + 2];
     const int j = lower_bound_hi16(outer, nu, phc);
@@ -594,29 +570,65 @@ __device__ __forceinline__ void add_tracklet(const Smem& S, const Region& R, int
         S.misc[kErr] = SBT_ERR_CAPACITY;
 }
 
-__device__ __forceinline__ void put_track(const Smem& S, int buf, int slot, int h0, int h1, int h2,
-                                          int key, int nh, int sk)
+__device__ __forceinline__ FTrack make_track(int h0, int h1, int h2, int key, int nh, int sk)
 {
-    const int i = buf * S.FC + slot;
-    S.f0[i] = (uint16_t)h0;
-    S.f1[i] = (uint16_t)h1;
-    S.f2[i] = (uint16_t)h2;
-    S.fkey[i] = (uint16_t)key;
-    S.fnh[i] = (uint8_t)nh;
-    S.fsk[i] = (uint8_t)sk;
+    FTrack T;
+    T.h0 = (uint16_t)h0;
+    T.h1 = (uint16_t)h1;
+    T.h2 = (uint16_t)h2;
+    T.key = (uint16_t)key;
+    T.nh = (uint8_t)nh;
+    T.sk = (uint8_t)sk;
+    T.cand = kNone;
+    T.sc = 0.0f;
+    return T;
+}
+
+// Following search of one forming track to module t and its claims: the new
+// hit, and for a 3-hit track also its three hits.  A 3-hit track with a
+// flagged hit cannot extend any more and is marked dead.
+__device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem& S, const Region& R,
+                                                 int t, unsigned long long tag, float sqrt_cut,
+                                                 FTrack& T)
+{
+    if (T.nh == 3 && (flagged(S, T.h0) || flagged(S, T.h1) || flagged(S, T.h2))) {
+        T.cand = kDead;
+        return;
+    }
+    int b;
+    float sc;
+    if (follow_best(C, S, R, t, T.h1, T.h2, sqrt_cut, b, sc)) {
+        T.cand = (uint16_t)b;
+        T.sc = sc;
+        const unsigned long long k = claim_key(tag, sc, T.key);
+        atomicMin(&R.claim[b], k);
+        if (T.nh == 3) {
+            atomicMin(&R.claim[T.h0], k);
+            atomicMin(&R.claim[T.h1], k);
+            atomicMin(&R.claim[T.h2], k);
+        }
+    } else {
+        T.cand = kNone;
+        T.sc = 0.0f;
+    }
 }
 
 // Iterative seeding and following.  Returns false (uniformly) on overflow.
+// Per module triplet (s, s+1, s+2) three phases separated by barriers:
+//   P0  work lists: unflagged middle hits of s+1, unflagged hits of s in order;
+//   P1  following of the forming tracks to t = s+3 with claims, and seeding
+//       (every new seed searches its own continuation at once);
+//   P2  resolution of the claims, flags, termination.
 // Claims carry a tag (64 - t) << 48 above (scatter bits, track key), so a
 // claim of an earlier step always compares larger than one of the current
 // step and the claim words need no reset between steps.
 template <int NT>
-__device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
+__device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const int M = C.M;
-    const int FC = S.FC;
     int* misc = S.misc;
+    const int cap = C.fcap > 0 ? min(C.fcap, forming_capacity(n)) : forming_capacity(n);
     const float sq_seed = sqrtf(C.S_seed), sq_follow = sqrtf(C.S_follow);
     uint32_t* list = R.keys;  // free after the sort
     if (tid == 0) {
@@ -626,13 +638,19 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
         misc[kNTl] = 0;
         misc[kErr] = 0;
         misc[kList] = 0;
+        misc[kNew] = 0;
     }
     __syncthreads();
     int cur = 0;
     for (int s = 0; s + 2 <= M - 1; ++s) {
         const int nxt = cur ^ 1;
-        // work lists: the unflagged middle hits of module s+1 (any order), and
-        // the unflagged hits of module s in sorted order (one warp, ballots)
+        FTrack* Fc = R.ft + cur * R.fstride;
+        FTrack* Fn = R.ft + nxt * R.fstride;
+        // P0
+        if (tid == 0) {
+            misc[kCnt0 + nxt] = 0;
+            misc[kNew] = 0;
+        }
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
         uint32_t* outer = list + (c1 - c0);
         for (int base = c0 + (tid & ~31); base < c1; base += NT) {
@@ -653,7 +671,7 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
                 const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
                 if (ok)
                     outer[nu + __popc(m & ((1u << lane) - 1u))] =
-                        ((uint32_t)S.phi[a] << 16) | (uint32_t)a;
+                        ((uint32_t)R.phi[a] << 16) | (uint32_t)a;
                 nu += __popc(m);
             }
             if (lane == 0) misc[kNOuter] = nu;
@@ -661,111 +679,85 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S)
         __syncthreads();
         const int nl = misc[kList];
         const int nu = misc[kNOuter];
-        // seeding over modules (s, s+1, s+2)
-        for (int i = tid; i < nl; i += NT) {
-            const int c = (int)list[i];
-            int a, b;
-            if (seed_for(C, S, R, s, c, outer, nu, sq_seed, a, b)) {
-                int slot = atomicAdd(&misc[kCnt0 + cur], 1);
-                if (slot < C.fcap)
-                    put_track(S, cur, slot, a, c, b, c, 3, 0);
-                else
-                    misc[kErr] = SBT_ERR_CAPACITY;
+        const int nold = misc[kCnt0 + cur];
+        const int t = s + 3;
+        const bool follow = t <= M - 1;
+        const unsigned long long tag = (unsigned long long)(64 - t) << 48;
+        // P1
+        for (int i = tid; i < nold + nl; i += NT) {
+            if (i < nold) {
+                if (follow) {
+                    FTrack T = Fc[i];
+                    follow_and_claim(C, S, R, t, tag, sq_follow, T);
+                    Fc[i] = T;
+                }
+            } else {
+                const int c = (int)list[i - nold];
+                int a, b;
+                if (seed_for(C, S, R, s, c, outer, nu, sq_seed, a, b)) {
+                    const int slot = nold + atomicAdd(&misc[kNew], 1);
+                    if (slot < cap) {
+                        FTrack T = make_track(a, c, b, c, 3, 0);
+                        if (follow) follow_and_claim(C, S, R, t, tag, sq_follow, T);
+                        Fc[slot] = T;
+                    } else {
+                        misc[kErr] = SBT_ERR_CAPACITY;
+                    }
+                }
             }
         }
         __syncthreads();
         if (misc[kErr]) return false;
-        const int nf = misc[kCnt0 + cur];
-        if (tid == 0) {
-            misc[kCnt0 + nxt] = 0;
-            misc[kList] = 0;
-        }
-        const int t = s + 3;
-        if (t <= M - 1) {
-            const unsigned long long tag = (unsigned long long)(64 - t) << 48;
-            // following: candidates and claims
+        const int nf = nold + misc[kNew];
+        if (tid == 0) misc[kList] = 0;
+        // P2
+        if (follow) {
             for (int f = tid; f < nf; f += NT) {
-                const int i = cur * FC + f;
-                const int nh = S.fnh[i];
-                const int h0 = S.f0[i], h1 = S.f1[i], h2 = S.f2[i];
-                uint16_t cand = kNone;
-                float sc = 0.0f;
-                if (nh == 3 && (flagged(S, h0) || flagged(S, h1) || flagged(S, h2))) {
-                    cand = kDead;
-                } else {
-                    int b;
-                    if (follow_best(C, S, R, t, h1, h2, sq_follow, b, sc)) {
-                        cand = (uint16_t)b;
-                        unsigned long long k = claim_key(tag, sc, S.fkey[i]);
-                        atomicMin(&R.claim[b], k);
-                        if (nh == 3) {
-                            atomicMin(&R.claim[h0], k);
-                            atomicMin(&R.claim[h1], k);
-                            atomicMin(&R.claim[h2], k);
-                        }
-                    }
-                }
-                S.fcand[f] = cand;
-                S.fsc[f] = sc;
-            }
-            __syncthreads();
-            // resolution: an extension is kept when it holds every hit it claimed
-            for (int f = tid; f < nf; f += NT) {
-                const uint16_t cand = S.fcand[f];
-                if (cand == kDead) continue;
-                const int i = cur * FC + f;
-                const int nh = S.fnh[i];
-                const int h0 = S.f0[i], h1 = S.f1[i], h2 = S.f2[i];
-                const int key = S.fkey[i];
-                int sk = S.fsk[i];
+                const FTrack T = Fc[f];
+                if (T.cand == kDead) continue;
                 bool won = false;
-                if (cand != kNone) {
-                    unsigned long long k = claim_key(tag, S.fsc[f], key);
-                    won = __ldcg(&R.claim[cand]) == k;
-                    if (won && nh == 3)
-                        won = __ldcg(&R.claim[h0]) == k && __ldcg(&R.claim[h1]) == k &&
-                              __ldcg(&R.claim[h2]) == k;
+                if (T.cand != kNone) {
+                    const unsigned long long k = claim_key(tag, T.sc, T.key);
+                    won = __ldcg(&R.claim[T.cand]) == k;
+                    if (won && T.nh == 3)
+                        won = __ldcg(&R.claim[T.h0]) == k && __ldcg(&R.claim[T.h1]) == k &&
+                              __ldcg(&R.claim[T.h2]) == k;
                 }
                 if (won) {
-                    set_flag(S, cand);
-                    if (nh == 3) {
-                        set_flag(S, h0);
-                        set_flag(S, h1);
-                        set_flag(S, h2);
-                        R.prev[h0] = kNone;
-                        R.prev[h1] = (uint16_t)h0;
-                        R.prev[h2] = (uint16_t)h1;
+                    set_flag(S, T.cand);
+                    if (T.nh == 3) {
+                        set_flag(S, T.h0);
+                        set_flag(S, T.h1);
+                        set_flag(S, T.h2);
+                        R.prev[T.h0] = kNone;
+                        R.prev[T.h1] = T.h0;
+                        R.prev[T.h2] = T.h1;
                     }
-                    R.prev[cand] = (uint16_t)h2;
-                    int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
-                    put_track(S, nxt, slot, h1, h2, cand, key, nh + 1, 0);
+                    R.prev[T.cand] = T.h2;
+                    const int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
+                    Fn[slot] = make_track(T.h1, T.h2, T.cand, T.key, T.nh + 1, 0);
+                } else if (T.sk + 1 >= 2) {
+                    if (T.nh >= 4)
+                        add_final(S, R, T.h2, T.nh);
+                    else
+                        add_tracklet(S, R, T.h0, T.h1, T.h2, T.key);
                 } else {
-                    sk += 1;
-                    if (sk >= 2) {
-                        if (nh >= 4)
-                            add_final(S, R, h2, nh);
-                        else
-                            add_tracklet(S, R, h0, h1, h2, key);
-                    } else {
-                        int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
-                        put_track(S, nxt, slot, h0, h1, h2, key, nh, sk);
-                    }
+                    const int slot = atomicAdd(&misc[kCnt0 + nxt], 1);
+                    Fn[slot] = make_track(T.h0, T.h1, T.h2, T.key, T.nh, T.sk + 1);
                 }
             }
-            __syncthreads();
-            cur = nxt;
         } else {
             // last iteration: every forming track is finished
             for (int f = tid; f < nf; f += NT) {
-                const int i = cur * FC + f;
-                const int nh = S.fnh[i];
-                if (nh >= 4)
-                    add_final(S, R, S.f2[i], nh);
+                const FTrack T = Fc[f];
+                if (T.nh >= 4)
+                    add_final(S, R, T.h2, T.nh);
                 else
-                    add_tracklet(S, R, S.f0[i], S.f1[i], S.f2[i], S.fkey[i]);
+                    add_tracklet(S, R, T.h0, T.h1, T.h2, T.key);
             }
-            __syncthreads();
         }
+        __syncthreads();
+        cur = nxt;
     }
     return misc[kErr] == 0;
 }
@@ -927,7 +919,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Work& W, c
         __syncthreads();
         return;
     }
-    if (!search_stage<NT>(C, R, S)) {
+    if (!search_stage<NT>(C, R, S, n)) {
         fail_event(e, SBT_ERR_CAPACITY, G, out);
         __syncthreads();
         return;
@@ -945,7 +937,7 @@ __global__ void __launch_bounds__(NT) k_reco_plain(DevConfig C, Inputs in, Work 
                                                     sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, C.nmax, C.fcap, NT);
+    Smem S = carve(smem_raw, C.nmax, NT);
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
@@ -959,7 +951,7 @@ __global__ void __launch_bounds__(NT) k_reco_persistent(DevConfig C, Inputs in, 
                                                          sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, C.nmax, C.fcap, NT);
+    Smem S = carve(smem_raw, C.nmax, NT);
     const int64_t hb = (int64_t)blockIdx.x * C.nmax;
     for (;;) {
         if (threadIdx.x == 0) S.misc[kEvent] = atomicAdd(&G.queue[0], 1);
@@ -1085,7 +1077,7 @@ __global__ void __launch_bounds__(NT) k_debug_sort(DevConfig C, Inputs in, Work 
                                                     int32_t* perm, int32_t* modoff, int32_t* status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, C.nmax, C.fcap, NT);
+    Smem S = carve(smem_raw, C.nmax, NT);
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
@@ -1099,7 +1091,7 @@ __global__ void __launch_bounds__(NT) k_debug_sort(DevConfig C, Inputs in, Work 
         return;
     }
     for (int p = threadIdx.x; p < n; p += NT) {
-        phi16[off + p] = S.phi[p];
+        phi16[off + p] = R.phi[p];
         perm[off + p] = __float_as_int(R.coords[p].w);
     }
     for (int m = threadIdx.x; m <= C.M; m += NT) modoff[(int64_t)e * (C.M + 1) + m] = S.modoff[m];
@@ -1118,7 +1110,7 @@ template <int NT>
 static cudaError_t plain_nt(const DevConfig& C, const Inputs& in, const Work& W, const Staging& G,
                             const sbt_tracks& out, cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    size_t sm = smem_bytes(C.nmax, NT);
     cudaError_t err = cudaFuncSetAttribute(k_reco_plain<NT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
@@ -1146,7 +1138,7 @@ cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream
 template <int NT>
 static int occupancy_nt(const DevConfig& C)
 {
-    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    size_t sm = smem_bytes(C.nmax, NT);
     if (cudaFuncSetAttribute(k_reco_persistent<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
         return 0;
@@ -1172,7 +1164,7 @@ static cudaError_t persistent_nt(const DevConfig& C, const Inputs& in, const Wor
                                  const Staging& G, const sbt_tracks& out, int blocks,
                                  cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    size_t sm = smem_bytes(C.nmax, NT);
     cudaError_t err = cudaFuncSetAttribute(k_reco_persistent<NT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
@@ -1223,7 +1215,7 @@ template <int NT>
 static cudaError_t debug_sort_nt(const DevConfig& C, const Inputs& in, const Work& W, uint16_t* phi16,
                                  int32_t* perm, int32_t* modoff, int32_t* status, cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, C.fcap, NT);
+    size_t sm = smem_bytes(C.nmax, NT);
     cudaError_t err = cudaFuncSetAttribute(k_debug_sort<NT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;

@@ -256,7 +256,7 @@ def sbt_reconstruct_noalloc(h: Handle, x, y, z, module, event_offsets, out: Trac
                             stream=None) -> TrackOutput:
     """sbt_reconstruct for callers that must not allocate device memory: the
     library allocates nothing (its workspace is a fixed array in its device
-    image, at most 524288 hits and 32768 events per call) and the caller passes
+    image, at most 524288 hits and 4096 events per call) and the caller passes
     preallocated outputs.  Calls that overlap on the GPU share that workspace
     and must be serialised."""
     f = lib().sbt_reconstruct_noalloc

@@ -213,6 +213,26 @@ def test_bad_module_and_oversize_events_are_reported(sbt):
         h.close()
 
 
+def test_forming_track_overflow_fails_only_that_event(sbt):
+    ev = synth.make_events(2, 20, workers=1)
+    h = sbt.sbt_create(MZ, sbt.default_config(max_forming_tracks=40, **CFG))
+    try:
+        for b in (False, True):
+            g = run_gpu(sbt, h, ev, b)
+            st = g["event_status"]
+            assert (st == sbt.SBT_ERR_CAPACITY).any() and (st == 0).any()
+            assert set(np.unique(st)) <= {0, sbt.SBT_ERR_CAPACITY}
+            for e in np.nonzero(st == 0)[0]:
+                lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+                one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], MZ,
+                                   oracle.config(**CFG))
+                t0, t1 = g["track_offsets"][e], g["track_offsets"][e + 1]
+                assert np.array_equal(g["track_hits"][g["hit_offsets"][t0]:g["hit_offsets"][t1]] - lo,
+                                      one.track_hits)
+    finally:
+        h.close()
+
+
 def test_output_capacity_overflow_is_reported(sbt, handle):
     ev = synth.make_events(2, 10, workers=1)
     x, y, z, m, off = to_dev(ev)
