@@ -272,11 +272,17 @@ def main():
     # per-kernel times (no graph, CUDA events on the launching stream)
     kms = sbt.sbt_profile_batched(h, *dev, out, reps=3)
     T, H = int(counts[0]), int(counts[1])
-    # algorithmic bytes of the persistent kernel: hits in (x, y, z, module: 16 B),
-    # event offsets, staged hit indices and track lengths out, per-event counts
-    alg_bytes = 16 * ev.n_hits + 4 * (ev.n_events + 1) + 4 * H + T + 12 * ev.n_events
+    # algorithmic bytes of the dominant kernel (the persistent search): sorted
+    # hits in (float4 coordinates and phi16: 18 B per hit), module offsets and
+    # event offsets, staged hit indices (4 B per track hit), track lengths,
+    # fits (1 + 20 B per track) and per-event counts out
+    alg_bytes = (18 * ev.n_hits + 4 * (ev.n_events + 1) + 4 * 53 * ev.n_events
+                 + 4 * H + 21 * T + 12 * ev.n_events)
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (kms[1] / 1e3) / 1e9
+    achieved = alg_bytes / (kms[2] / 1e3) / 1e9
+    # the sort kernel streams the inputs (16 B per hit) and writes the sorted hits (18 B per hit)
+    sort_bytes = 16 * ev.n_hits + 4 * (ev.n_events + 1) + 18 * ev.n_hits + 4 * 54 * ev.n_events
+    sort_gbs = sort_bytes / (kms[1] / 1e3) / 1e9
 
     plain = None
     if not args.no_plain:
@@ -358,9 +364,10 @@ def main():
             "e2e": e2e,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_reco_persistent", "kernel_ms": kms[1],
-                         "kernel_ms_all": {"order": kms[0], "reco": kms[1], "scan": kms[2],
-                                           "consolidate": kms[3]}},
+                         "kernel": "k_search_persistent", "kernel_ms": kms[2],
+                         "kernel_ms_all": {"order": kms[0], "sort": kms[1], "search": kms[2],
+                                           "scan": kms[3], "consolidate": kms[4]},
+                         "sort_kernel": {"achieved_gbs": sort_gbs, "frac": sort_gbs / peak}},
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clk,

@@ -25,7 +25,7 @@
  *   - A handle may be used from one host thread at a time, and its calls must
  *     not overlap on the GPU (they share the handle's workspace): use one
  *     handle per concurrent stream.
- *   - Hit index types: the event-local hit count is at most 65533; batch hit
+ *   - Hit index types: the event-local hit count is at most 16384; batch hit
  *     indices and offsets are int32.
  */
 #ifndef SBT_H
@@ -66,7 +66,7 @@ typedef struct {
     float max_scatter_follow;    /* following scatter cut, mm^2; default 0.04 */
     float max_chi2_tracklet;     /* tracklet filter chi2 cut; default 20 */
     float hit_sigma;             /* hit resolution for chi2, mm; default 0.012 */
-    int32_t max_hits_per_event;  /* events with more hits get SBT_ERR_CAPACITY; default 16384, <= 65533 */
+    int32_t max_hits_per_event;  /* events with more hits get SBT_ERR_CAPACITY; default and maximum 16384 */
     int32_t max_forming_tracks;  /* forming tracks alive per event: n_hits/12 + 64; a positive value lowers the bound */
     int32_t threads_per_block;   /* 64, 128 or 256; 0 = 128 (batched: autotuned value if any) */
 } sbt_config;
@@ -196,8 +196,8 @@ sbt_status sbt_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* 
 /*
  * Measurement helper: runs the batched sequence `reps` times without a graph,
  * timing each kernel with CUDA events on `stream`, and writes the mean
- * milliseconds per launch to ms[4] (host): ordering kernel, persistent
- * reconstruction kernel, scan, consolidation.  Synchronous.
+ * milliseconds per launch to ms[5] (host): ordering kernel, sort kernel,
+ * persistent search kernel, scan, consolidation.  Synchronous.
  */
 sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, const float* z,
                                const int32_t* module, const int32_t* event_offsets,
@@ -212,7 +212,7 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
  * application that owns the device memory pool.  The paper has no
  * counterpart; it computes exactly what sbt_reconstruct computes.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *     workspace is a fixed array of about 38 MB inside the library's device
+ *     workspace is a fixed array of about 39 MB inside the library's device
  *     image, held by every GPU that loads the library until the process exits.
  *   - At most 524288 hits and 4096 events per call; larger batches return
  *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).

@@ -66,20 +66,31 @@ size_t carve_work(void* base, int64_t hits, int64_t regions, Work* W)
 {
     Carver c(base);
     Work w;
-    w.coords = c.take<float4>(hits);
-    w.phi = c.take<uint16_t>(hits);
-    w.ft = c.take<FTrack>(forming_entries(hits, regions));
-    w.keys = c.take<uint32_t>(hits);
-    w.idxA = c.take<uint16_t>(hits);
-    w.idxB = c.take<uint16_t>(hits);
+    w.list = c.take<uint32_t>(hits);
+    w.mark = c.take<uint16_t>(hits);
+    w.pos = c.take<uint16_t>(hits);
     w.prev = c.take<uint16_t>(hits);
     w.claim = c.take<unsigned long long>(hits);
+    w.ft = c.take<FTrack>(forming_entries(hits, regions));
     w.tracklets = c.take<unsigned long long>(tracklet_entries(hits, regions));
     w.tl_q = c.take<uint32_t>(tracklet_entries(hits, regions));
     w.finals = c.take<uint32_t>(final_entries(hits, regions));
     w.fin_rank = c.take<int32_t>(final_entries(hits, regions));
     w.fin_start = c.take<int32_t>(final_entries(hits, regions));
     if (W) *W = w;
+    return c.off + 256;
+}
+
+// Sorted hits of a batch (see Sorted).
+size_t carve_sorted(void* base, int64_t n_hits, int64_t n_events, int M, Sorted* O)
+{
+    Carver c(base);
+    Sorted o;
+    o.coords = c.take<float4>(n_hits);
+    o.phi = c.take<uint16_t>(n_hits);
+    o.modoff = c.take<int32_t>(n_events * (M + 1));
+    o.status = c.take<int32_t>(n_events);
+    if (O) *O = o;
     return c.off + 256;
 }
 
@@ -118,7 +129,7 @@ struct sbt_handle {
     int device = 0;
     int sm_count = 0;
     std::string err;
-    Arena plain_arena, pers_arena, stage_arena, host_arena, misc_arena;
+    Arena plain_arena, pers_arena, stage_arena, host_arena, misc_arena, sorted_arena;
     int tuned_threads = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -181,6 +192,15 @@ Inputs make_inputs(const float* x, const float* y, const float* z, const int32_t
     return in;
 }
 
+sbt_status ensure_sorted(sbt_handle* h, int64_t n_hits, int64_t n_events, Sorted* O)
+{
+    size_t need = carve_sorted(nullptr, n_hits, n_events, h->C.M, nullptr);
+    cudaError_t e = h->sorted_arena.reserve(need);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sorted-hit allocation");
+    carve_sorted(h->sorted_arena.base, n_hits, n_events, h->C.M, O);
+    return SBT_OK;
+}
+
 sbt_status ensure_staging(sbt_handle* h, int64_t n_hits, int64_t n_events, Staging* S)
 {
     size_t need = carve_staging(nullptr, n_hits, n_events, nullptr);
@@ -206,14 +226,16 @@ sbt_status ensure_persistent(sbt_handle* h, int blocks, Work* W)
     return SBT_OK;
 }
 
-// Enqueue the batched sequence (order, persistent search, scan, consolidation).
-sbt_status enqueue_batched(sbt_handle* h, const Inputs& in, const Staging& S, const Work& W,
-                           const sbt_tracks& out, int threads, int blocks, cudaStream_t st)
+// Enqueue the batched sequence (order, sort, persistent search, scan, consolidation).
+sbt_status enqueue_batched(sbt_handle* h, const Inputs& in, const Sorted& O, const Staging& S,
+                           const Work& W, const sbt_tracks& out, int threads, int blocks,
+                           cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(S.queue, 0, 4 * sizeof(int32_t), st);
     if (e == cudaSuccess && in.n_events > 0) e = launch_order(in, S, st);
+    if (e == cudaSuccess && in.n_events > 0) e = launch_sort(h->C, in, O, st);
     if (e == cudaSuccess && in.n_events > 0)
-        e = launch_persistent(h->C, in, W, S, out, threads, std::min(blocks, in.n_events), st);
+        e = launch_persistent(h->C, in, O, W, S, out, threads, std::min(blocks, in.n_events), st);
     if (e == cudaSuccess) e = launch_finish(h->C, in, S, out, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "batched launch");
     return SBT_OK;
@@ -293,7 +315,7 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
         delete h;
         return SBT_ERR_CUDA;
     }
-    if (smem_bytes(h->C.nmax, 256) > (size_t)max_optin) {
+    if (sort_smem_bytes(h->C.nmax) > (size_t)max_optin || smem_bytes(h->C.nmax, 256) > (size_t)max_optin) {
         g_create_error = "max_hits_per_event exceeds shared memory";
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         delete h;
@@ -310,6 +332,7 @@ sbt_status sbt_destroy(sbt_handle* h)
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->plain_arena.release();
+    h->sorted_arena.release();
     h->pers_arena.release();
     h->stage_arena.release();
     h->host_arena.release();
@@ -332,17 +355,20 @@ sbt_status sbt_reconstruct(sbt_handle* h, const float* x, const float* y, const 
     if (st != SBT_OK || !out) return st != SBT_OK ? st : SBT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     Staging S;
+    Sorted O;
     if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
+    if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
     size_t need = carve_work(nullptr, n_hits, n_events, nullptr);
     cudaError_t e = h->plain_arena.reserve(need);
     if (e != cudaSuccess) return cuda_fail(h, e, "workspace allocation");
     Work W;
     carve_work(h->plain_arena.base, n_hits, n_events, &W);
     Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
-    e = launch_plain(h->C, in, W, S, *out, default_threads(h, false), s);
+    e = launch_sort(h->C, in, O, s);
+    if (e == cudaSuccess) e = launch_plain(h->C, in, O, W, S, *out, default_threads(h, false), s);
     if (e == cudaSuccess) e = launch_finish(h->C, in, S, *out, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "plain launch");
-    h->launches_last = n_events > 0 ? 3 : 1;
+    h->launches_last = n_events > 0 ? 4 : 2;
     return SBT_OK;
 }
 
@@ -358,10 +384,13 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
     const int blocks = persistent_blocks(h, threads);
     Staging S;
     Work W;
+    Sorted O;
     const void* old_stage = h->stage_arena.base;
     const void* old_pers = h->pers_arena.base;
+    const void* old_sorted = h->sorted_arena.base;
     if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
     if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) return st;
+    if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
     GraphKey k{};
     const void* ptrs[13] = {x, y, z, module, event_offsets, out->track_offsets, out->hit_offsets,
                             out->track_hits, out->params, out->chi2, out->ndof, out->event_status,
@@ -373,7 +402,8 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
     k.vals[3] = out->cap_hits;
     k.vals[4] = threads;
     k.vals[5] = blocks;
-    const bool moved = old_stage != h->stage_arena.base || old_pers != h->pers_arena.base;
+    const bool moved = old_stage != h->stage_arena.base || old_pers != h->pers_arena.base ||
+                       old_sorted != h->sorted_arena.base;
     if (!h->exec || !h->have_key || moved || !(k == h->key)) {
         if (h->exec) {
             cudaGraphExecDestroy(h->exec);
@@ -384,7 +414,7 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(h, e, "graph capture begin");
-        st = enqueue_batched(h, in, S, W, *out, threads, blocks, h->cap_stream);
+        st = enqueue_batched(h, in, O, S, W, *out, threads, blocks, h->cap_stream);
         e = cudaStreamEndCapture(h->cap_stream, &g);
         if (st != SBT_OK) {
             if (g) cudaGraphDestroy(g);
@@ -402,7 +432,7 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
     }
     cudaError_t e = cudaGraphLaunch(h->exec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
-    h->launches_last = n_events > 0 ? 4 : 2;
+    h->launches_last = n_events > 0 ? 5 : 2;
     return SBT_OK;
 }
 
@@ -491,13 +521,18 @@ sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const flo
     if (st != SBT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     Staging S;
+    Sorted O;
     if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
-    cudaError_t e = h->misc_arena.reserve(sizeof(int32_t) * ((size_t)n_events + 8));
+    if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
+    cudaError_t e = h->misc_arena.reserve(std::max(sizeof(int32_t) * ((size_t)n_events + 8), h->misc_arena.bytes));
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune allocation");
     sbt_tracks scratch_out;
     std::memset(&scratch_out, 0, sizeof(scratch_out));
     scratch_out.event_status = (int32_t*)h->misc_arena.base;
     Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
+    e = launch_order(in, S, s);
+    if (e == cudaSuccess) e = launch_sort(h->C, in, O, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -511,10 +546,9 @@ sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const flo
         float tot = 0.0f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
             e = cudaMemsetAsync(S.queue, 0, 16, s);
-            if (e == cudaSuccess) e = launch_order(in, S, s);
             if (e == cudaSuccess) e = cudaEventRecord(a, s);
             if (e == cudaSuccess)
-                e = launch_persistent(h->C, in, W, S, scratch_out, threads,
+                e = launch_persistent(h->C, in, O, W, S, scratch_out, threads,
                                       std::min(blocks, std::max(n_events, 1)), s);
             if (e == cudaSuccess) e = cudaEventRecord(b, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(b);
@@ -534,6 +568,11 @@ sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const flo
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
     h->tuned_threads = best;
     if (chosen) *chosen = best;
+    if (h->exec) {  // the workspace may have moved
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+        h->have_key = false;
+    }
     return SBT_OK;
 }
 
@@ -566,15 +605,12 @@ sbt_status sbt_debug_sort(sbt_handle* h, const float* x, const float* y, const i
     sbt_status st = check_inputs(h, x, y, x, module, event_offsets, n_events, n_hits, nullptr);
     if (st != SBT_OK) return st;
     if (!phi16 || !perm || !module_offsets) return fail(h, SBT_ERR_ARG, "NULL output");
-    size_t need = carve_work(nullptr, n_hits, n_events, nullptr);
-    cudaError_t e = h->plain_arena.reserve(need);
-    if (e == cudaSuccess) e = h->misc_arena.reserve(std::max(sizeof(int32_t) * ((size_t)n_events + 8), h->misc_arena.bytes));
-    if (e != cudaSuccess) return cuda_fail(h, e, "workspace allocation");
-    Work W;
-    carve_work(h->plain_arena.base, n_hits, n_events, &W);
+    Sorted O;
+    if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
     Inputs in = make_inputs(x, y, x, module, event_offsets, n_events, n_hits);
-    e = launch_debug_sort(h->C, in, W, phi16, perm, module_offsets, (int32_t*)h->misc_arena.base,
-                          default_threads(h, false), (cudaStream_t)stream);
+    cudaError_t e = launch_sort(h->C, in, O, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = launch_debug_sort_copy(h->C, in, O, phi16, perm, module_offsets, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "debug sort launch");
     return SBT_OK;
 }
@@ -598,41 +634,44 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
     const int blocks = persistent_blocks(h, threads);
     Staging S;
     Work W;
+    Sorted O;
     if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
     if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) return st;
-    // invalidate the graph cache: the arenas may have moved
-    if (h->exec) {
+    if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
+    if (h->exec) {  // the workspace may have moved
         cudaGraphExecDestroy(h->exec);
         h->exec = nullptr;
         h->have_key = false;
     }
     Inputs in = make_inputs(x, y, z, module, event_offsets, n_events, n_hits);
-    cudaEvent_t ev[5];
-    for (int i = 0; i < 5; i++) cudaEventCreate(&ev[i]);
-    double acc[4] = {0, 0, 0, 0};
+    cudaEvent_t ev[6];
+    for (int i = 0; i < 6; i++) cudaEventCreate(&ev[i]);
+    double acc[5] = {0, 0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < reps && e == cudaSuccess; r++) {
         e = cudaMemsetAsync(S.queue, 0, 16, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
         if (e == cudaSuccess && n_events > 0) e = launch_order(in, S, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
-        if (e == cudaSuccess && n_events > 0)
-            e = launch_persistent(h->C, in, W, S, *out, threads, std::min(blocks, n_events), s);
+        if (e == cudaSuccess && n_events > 0) e = launch_sort(h->C, in, O, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
-        if (e == cudaSuccess) e = launch_scan(in, S, *out, s);
+        if (e == cudaSuccess && n_events > 0)
+            e = launch_persistent(h->C, in, O, W, S, *out, threads, std::min(blocks, n_events), s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
-        if (e == cudaSuccess) e = launch_consolidate(h->C, in, S, *out, s);
+        if (e == cudaSuccess) e = launch_scan(in, S, *out, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-        for (int k = 0; k < 4 && e == cudaSuccess; k++) {
+        if (e == cudaSuccess) e = launch_consolidate(h->C, in, S, *out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
+        for (int k = 0; k < 5 && e == cudaSuccess; k++) {
             float t = 0.0f;
             cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
             acc[k] += t;
         }
     }
-    for (int i = 0; i < 5; i++) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 6; i++) cudaEventDestroy(ev[i]);
     if (e != cudaSuccess) return cuda_fail(h, e, "profile");
-    for (int k = 0; k < 4; k++) ms[k] = (float)(acc[k] / reps);
+    for (int k = 0; k < 5; k++) ms[k] = (float)(acc[k] / reps);
     return SBT_OK;
 }
 

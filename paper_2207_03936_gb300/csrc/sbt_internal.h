@@ -10,7 +10,7 @@
 namespace sbt {
 
 constexpr int kMaxModules = 64;
-constexpr int kMaxHitsPerEvent = 65533;  // event-local indices are uint16; 0xFFFF and 0xFFFE are markers
+constexpr int kMaxHitsPerEvent = 16384;  // the per-event sort runs in shared memory
 
 // Method constants and per-event capacities, passed to kernels by value.
 struct DevConfig {
@@ -47,20 +47,27 @@ __host__ __device__ inline int forming_capacity(int n) { return n / 12 + 64; }
 __host__ __device__ inline int64_t forming_base(int64_t hb, int64_t r) { return 2 * (hb / 12 + 72 * r); }
 inline int64_t forming_entries(int64_t hits, int64_t regions) { return 2 * (hits / 12 + 72 * regions) + 2; }
 
-// Per-region scratch (a region is an event in the plain launch, a resident
-// block in the persistent launch).  Region r with hit base hb and capacity
-// cap owns per-hit arrays [hb, hb + cap), tracklets from hb/4 + r (cap/4 + 1
-// entries), final-track records from hb/3 + r (cap/3 + 1 entries) and
-// forming-track slots from forming_base(hb, r) (2 (cap/12 + 72) entries).
+// Sorted hits of every event, written by the sort kernel (indexed like the
+// inputs: event e owns [event_offsets[e], event_offsets[e+1])).
+struct Sorted {
+    float4* coords;   // (x, y, z, event-local input index as int bits) by sorted position
+    uint16_t* phi;    // phi16 by sorted position
+    int32_t* modoff;  // [n_events * (n_modules + 1)] event-local module offsets
+    int32_t* status;  // [n_events] SBT_OK, SBT_ERR_ARG or SBT_ERR_CAPACITY after the sort
+};
+
+// Per-region scratch of the search (a region is an event in the plain launch,
+// a resident block in the persistent launch).  Region r with hit base hb and
+// capacity cap owns per-hit arrays [hb, hb + cap), tracklets from hb/4 + r
+// (cap/4 + 1 entries), final-track records from hb/3 + r (cap/3 + 1 entries)
+// and forming-track slots from forming_base(hb, r) (2 (cap/12 + 72) entries).
 struct Work {
-    float4* coords;              // sorted (x, y, z, input index as int bits)
-    uint16_t* phi;               // phi16 by sorted position
-    FTrack* ft;                  // forming tracks, two buffers
-    uint32_t* keys;              // (module << 16 | phi16) by input index
-    uint16_t* idxA;              // radix ping buffer; canonical-order marks afterwards
-    uint16_t* idxB;              // radix pong buffer; final sorted order
+    uint32_t* list;              // seeding work lists
+    uint16_t* mark;              // canonical-order marks by input index
+    uint16_t* pos;               // track hit positions in output order
     uint16_t* prev;              // previous hit of a track, by sorted position
     unsigned long long* claim;   // hit claims (tagged keys), by sorted position
+    FTrack* ft;                  // forming tracks, two buffers
     unsigned long long* tracklets;
     uint32_t* tl_q;
     uint32_t* finals;            // last hit | nhits << 16
@@ -87,12 +94,14 @@ inline int64_t tracklet_entries(int64_t hits, int64_t regions) { return hits / 4
 inline int64_t final_entries(int64_t hits, int64_t regions) { return hits / 3 + regions + 1; }
 
 size_t smem_bytes(int nmax, int threads);
+size_t sort_smem_bytes(int nmax);
 
 // Launchers (sbt_reco.cu).  All asynchronous on `stream`.
-cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Work& W, const Staging& S,
-                         const sbt_tracks& out, int threads, cudaStream_t stream);
+cudaError_t launch_sort(const DevConfig& C, const Inputs& in, const Sorted& O, cudaStream_t stream);
+cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
+                         const Staging& S, const sbt_tracks& out, int threads, cudaStream_t stream);
 cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream);
-cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Work& W,
+cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                               const Staging& S, const sbt_tracks& out, int threads, int blocks,
                               cudaStream_t stream);
 cudaError_t launch_finish(const DevConfig& C, const Inputs& in, const Staging& S,
@@ -101,13 +110,12 @@ cudaError_t launch_scan(const Inputs& in, const Staging& S, const sbt_tracks& ou
                         cudaStream_t stream);
 cudaError_t launch_consolidate(const DevConfig& C, const Inputs& in, const Staging& S,
                                const sbt_tracks& out, cudaStream_t stream);
-cudaError_t launch_debug_sort(const DevConfig& C, const Inputs& in, const Work& W,
-                              uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
-                              int32_t* status, int threads, cudaStream_t stream);
+cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const Sorted& O,
+                                   uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
+                                   cudaStream_t stream);
 cudaError_t launch_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out,
                                cudaStream_t stream);
 int persistent_blocks_per_sm(const DevConfig& C, int threads);
-int plain_kernel_count();
 
 // Adjoint (sbt_adjoint.cu).
 struct AdjointWork {

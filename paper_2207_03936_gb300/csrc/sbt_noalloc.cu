@@ -25,10 +25,11 @@ constexpr int64_t kNoAllocMaxEvents = int64_t(1) << 12; // 4096 events
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Offsets of the workspace arrays (the Work and Staging layouts for
+// Offsets of the workspace arrays (the Sorted, Work and Staging layouts for
 // kNoAllocMaxHits hits and kNoAllocMaxEvents events), each 256-byte aligned.
 struct Layout {
-    size_t coords, phi, ft, keys, idxA, idxB, prev, claim, tracklets, tl_q, finals, fin_rank, fin_start;
+    size_t coords, phi, modoff, status;
+    size_t list, mark, pos, prev, claim, ft, tracklets, tl_q, finals, fin_rank, fin_start;
     size_t hits, len, fit, chi2, ntracks, nhits, track_base, hit_base, order, queue, total;
 };
 
@@ -40,12 +41,14 @@ constexpr Layout make_layout()
     size_t o = 0;
     L.coords = o;     o = align256(o + 16 * (size_t)H);
     L.phi = o;        o = align256(o + 2 * (size_t)H);
-    L.ft = o;         o = align256(o + 16 * (size_t)(2 * (H / 12 + 72 * E) + 2));
-    L.keys = o;       o = align256(o + 4 * (size_t)H);
-    L.idxA = o;       o = align256(o + 2 * (size_t)H);
-    L.idxB = o;       o = align256(o + 2 * (size_t)H);
+    L.modoff = o;     o = align256(o + 4 * (size_t)E * (kMaxModules + 1));
+    L.status = o;     o = align256(o + 4 * (size_t)E);
+    L.list = o;       o = align256(o + 4 * (size_t)H);
+    L.mark = o;       o = align256(o + 2 * (size_t)H);
+    L.pos = o;        o = align256(o + 2 * (size_t)H);
     L.prev = o;       o = align256(o + 2 * (size_t)H);
     L.claim = o;      o = align256(o + 8 * (size_t)H);
+    L.ft = o;         o = align256(o + 16 * (size_t)(2 * (H / 12 + 72 * E) + 2));
     L.tracklets = o;  o = align256(o + 8 * (size_t)TL);
     L.tl_q = o;       o = align256(o + 4 * (size_t)TL);
     L.finals = o;     o = align256(o + 4 * (size_t)FN);
@@ -67,7 +70,7 @@ constexpr Layout make_layout()
 
 constexpr Layout kLayout = make_layout();
 
-// The workspace (about 38 MB).  In host code this name is only a host-side
+// The workspace (about 39 MB).  In host code this name is only a host-side
 // stand-in: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_workspace[kLayout.total];
 
@@ -130,15 +133,18 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
         return SBT_ERR_CUDA;
     }
     const Layout& L = kLayout;
+    Sorted O;
+    O.coords = (float4*)(base + L.coords);
+    O.phi = (uint16_t*)(base + L.phi);
+    O.modoff = (int32_t*)(base + L.modoff);
+    O.status = (int32_t*)(base + L.status);
     Work W;
-    W.coords = (float4*)(base + L.coords);
-    W.phi = (uint16_t*)(base + L.phi);
-    W.ft = (FTrack*)(base + L.ft);
-    W.keys = (uint32_t*)(base + L.keys);
-    W.idxA = (uint16_t*)(base + L.idxA);
-    W.idxB = (uint16_t*)(base + L.idxB);
+    W.list = (uint32_t*)(base + L.list);
+    W.mark = (uint16_t*)(base + L.mark);
+    W.pos = (uint16_t*)(base + L.pos);
     W.prev = (uint16_t*)(base + L.prev);
     W.claim = (unsigned long long*)(base + L.claim);
+    W.ft = (FTrack*)(base + L.ft);
     W.tracklets = (unsigned long long*)(base + L.tracklets);
     W.tl_q = (uint32_t*)(base + L.tl_q);
     W.finals = (uint32_t*)(base + L.finals);
@@ -155,9 +161,10 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     S.hit_base = (int32_t*)(base + L.hit_base);
     S.order = (int32_t*)(base + L.order);
     S.queue = (int32_t*)(base + L.queue);
-    // Every array the kernels read is written earlier in the same call (hit
-    // claims and marks per event in the sort stage, counts per event before
-    // the scan), so nothing needs clearing between calls.
+    // Every array the kernels read is written earlier in the same call (sorted
+    // hits and status by the sort kernel, claims and marks per event before
+    // they are used, counts per event before the scan), so nothing needs
+    // clearing between calls.
     Inputs in;
     in.x = x;
     in.y = y;
@@ -168,7 +175,8 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     in.n_hits = n_hits;
     cudaStream_t s = (cudaStream_t)stream;
     const DevConfig& C = handle_device_config(h);
-    e = launch_plain(C, in, W, S, *out, handle_plain_threads(h), s);
+    e = launch_sort(C, in, O, s);
+    if (e == cudaSuccess) e = launch_plain(C, in, O, W, S, *out, handle_plain_threads(h), s);
     if (e == cudaSuccess) e = launch_finish(C, in, S, *out, s);
     if (e != cudaSuccess) {
         handle_set_error(h, std::string("noalloc launch: ") + cudaGetErrorString(e));

@@ -1,18 +1,18 @@
 // Search-by-triplet reconstruction kernels for sm_103a.
 //
-// One thread block reconstructs one event (Table 1 of the paper: events map
-// to blocks, hits and forming tracks to threads).  Per event:
-//   1. phi16 of every hit and a stable LSD radix sort of (module, phi16) in
-//      three passes (section "Sort by phi"); sorted hits are gathered into
-//      an AoS float4 array (x, y, z, input index);
-//   2. for every module triplet (s, s+1, s+2): seeding over the unflagged
+// Events map to thread blocks, hits and forming tracks to threads (Table 1
+// of the paper).  Two kernels per event:
+//   1. k_sort: phi16 of every hit and a stable LSD radix sort of (module,
+//      phi16) in three passes in shared memory (section "Sort by phi"); the
+//      sorted hits are written as AoS float4 (x, y, z, input index) + phi16;
+//   2. k_search_*: for every module triplet (s, s+1, s+2): seeding over the unflagged
 //      middle hits, then following of every forming track to module s+3 with
 //      one-round claims on the hits, flags, and termination after two misses
 //      (section "Track seeding and track following"); barriers separate the
 //      stages as the paper's flagged-hits dependency requires;
-//   3. the tracklet filter (section "Tracklet filter");
-//   4. canonical ordering of the tracks by smallest input hit index and
-//      staging of their hit lists.
+//      then the tracklet filter (section "Tracklet filter"), canonical
+//      ordering of the tracks by smallest input hit index, staging of their
+//      hit lists and the least-squares fit of every track.
 // A device-wide scan and a consolidation kernel then build the CSR output
 // and fit every track (section "Results", data consolidation).
 //
@@ -21,6 +21,7 @@
 // exact track set of the plain definition.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -151,36 +152,30 @@ enum Misc {
     kNew = 8, kMiscN = 32
 };
 
-// Per-block shared memory: flag bits, module offsets, radix histograms and
-// counters.  Everything sized by the event's hit count lives in the block's
-// global scratch region (L1-resident), so a block needs only a few KB and
-// many events are in flight per SM.
+// Per-block shared memory of the search: flag bits, module offsets, counters.
+// Everything sized by the event lives in global scratch (L1-resident), so a
+// block needs about 2 KB plus n/8 bytes and many events are in flight per SM.
 struct Smem {
     uint32_t* flag;     // one bit per sorted position
     int* modoff;
-    int* hist;          // radix histograms [warps][256]
     int* misc;
-    int* tot;           // [256]
-    int* base;          // [256]
     int* wsum;          // [33]
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct Plan {
-    size_t flag, modoff, hist, misc, tot, base, wsum, total;
+    size_t flag, modoff, misc, wsum, total;
 };
 
 __host__ __device__ inline Plan make_plan(int nmax, int threads)
 {
+    (void)threads;
     Plan p;
     size_t o = 0;
     p.flag = o;     o = align16(o + 4 * (((size_t)nmax + 31) / 32));
     p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
-    p.hist = o;     o = align16(o + 4 * 256 * (size_t)(threads / 32));
     p.misc = o;     o = align16(o + 4 * kMiscN);
-    p.tot = o;      o = align16(o + 4 * 256);
-    p.base = o;     o = align16(o + 4 * 256);
     p.wsum = o;     o = align16(o + 4 * 40);
     p.total = o;
     return p;
@@ -194,10 +189,7 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
     Smem S;
     S.flag = (uint32_t*)(raw + p.flag);
     S.modoff = (int*)(raw + p.modoff);
-    S.hist = (int*)(raw + p.hist);
     S.misc = (int*)(raw + p.misc);
-    S.tot = (int*)(raw + p.tot);
-    S.base = (int*)(raw + p.base);
     S.wsum = (int*)(raw + p.wsum);
     return S;
 }
@@ -205,12 +197,13 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
 __device__ __forceinline__ bool flagged(const Smem& S, int p) { return (S.flag[p >> 5] >> (p & 31)) & 1u; }
 __device__ __forceinline__ void set_flag(const Smem& S, int p) { atomicOr(&S.flag[p >> 5], 1u << (p & 31)); }
 
+// What one event's search sees: its sorted hits (read-only) and its scratch.
 struct Region {
-    float4* coords;
-    uint16_t* phi;
-    uint32_t* keys;     // sort keys; afterwards the seeding work lists
-    uint16_t* idxA;     // radix buffer; afterwards canonical-order marks
-    uint16_t* idxB;     // radix buffer; afterwards track hit positions in order
+    const float4* coords;
+    const uint16_t* phi;
+    uint32_t* list;
+    uint16_t* mark;
+    uint16_t* pos;
     uint16_t* prev;
     unsigned long long* claim;
     unsigned long long* tracklets;
@@ -223,14 +216,15 @@ struct Region {
     int fstride;
 };
 
-__device__ inline Region region_of(const Work& W, int64_t hb, int64_t r, int cap)
+__device__ inline Region region_of(const Sorted& O, int off, const Work& W, int64_t hb, int64_t r,
+                                   int cap)
 {
     Region R;
-    R.coords = W.coords + hb;
-    R.phi = W.phi + hb;
-    R.keys = W.keys + hb;
-    R.idxA = W.idxA + hb;
-    R.idxB = W.idxB + hb;
+    R.coords = O.coords + off;
+    R.phi = O.phi + off;
+    R.list = W.list + hb;
+    R.mark = W.mark + hb;
+    R.pos = W.pos + hb;
     R.prev = W.prev + hb;
     R.claim = W.claim + hb;
     R.tracklets = W.tracklets + hb / 4 + r;
@@ -276,20 +270,44 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
     return res;
 }
 
-// -------------------------------------------------------------- sorting ---
+// ------------------------------------------------------------- sorting ---
 
-// One stable counting pass over `bits` bits of keys[src[i]] >> shift.
-// Warp w owns the contiguous chunk w of the input; ranks among equal digits
-// inside a warp come from match/popc, so the pass is stable.
-template <int NT>
-__device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* dst, int n,
-                           int shift, int bits, const Smem& S, int* modoff_out, int M)
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+
+// Shared memory of the sort kernel: keys and indices ping-pong (12 B per hit)
+// and the per-warp digit histograms.
+__host__ __device__ inline size_t sort_layout(int nmax, size_t* off_kb, size_t* off_ia,
+                                              size_t* off_ib, size_t* off_hist, size_t* off_misc)
 {
-    constexpr int NW = NT / 32;
+    size_t o = 0;
+    const size_t ka = o;  o = align16(o + 4 * (size_t)nmax);
+    *off_kb = o;          o = align16(o + 4 * (size_t)nmax);
+    *off_ia = o;          o = align16(o + 2 * (size_t)nmax);
+    *off_ib = o;          o = align16(o + 2 * (size_t)nmax);
+    *off_hist = o;        o = align16(o + 4 * 256 * (size_t)kSortWarps);
+    *off_misc = o;        o = align16(o + 4 * (256 + 256 + 40 + kMiscN));
+    (void)ka;
+    return o;
+}
+
+size_t sort_smem_bytes(int nmax)
+{
+    size_t a, b, c, d, e;
+    return sort_layout(nmax, &a, &b, &c, &d, &e);
+}
+
+// One stable counting pass over `bits` bits of the keys (key >> shift): the
+// keys travel with their indices.  Warp w owns the contiguous chunk w of the
+// input; ranks among equal digits inside a warp come from match/popc.
+__device__ void radix_pass(const uint32_t* ks, const uint16_t* is, uint32_t* kd, uint16_t* id,
+                           int n, int shift, int bits, int* hist, int* tot, int* base,
+                           int* modoff_out, int M)
+{
+    constexpr int NT = kSortThreads, NW = kSortWarps;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nd = 1 << bits;
     const unsigned lt = (1u << lane) - 1u;
-    int* hist = S.hist;
     for (int k = tid; k < NW * 256; k += NT) hist[k] = 0;
     __syncthreads();
     const int chunk = (n + NW - 1) / NW;
@@ -298,7 +316,7 @@ __device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* 
     for (int b = beg; b < end; b += 32) {
         int j = b + lane;
         bool v = j < end;
-        unsigned d = v ? ((keys[src[j]] >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
+        unsigned d = v ? ((ks[j] >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
         unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
         if (v && lane == __ffs(peers) - 1) hist[warp * 256 + d] += __popc(peers);
         __syncwarp();
@@ -307,13 +325,13 @@ __device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* 
     for (int d = tid; d < nd; d += NT) {
         int s = 0;
         for (int w = 0; w < NW; w++) s += hist[w * 256 + d];
-        S.tot[d] = s;
+        tot[d] = s;
     }
     __syncthreads();
     if (warp == 0) {
         const int per = nd / 32;
         int s = 0;
-        for (int k = 0; k < per; k++) s += S.tot[lane * per + k];
+        for (int k = 0; k < per; k++) s += tot[lane * per + k];
         int incl = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -322,13 +340,13 @@ __device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* 
         }
         int ex = incl - s;
         for (int k = 0; k < per; k++) {
-            S.base[lane * per + k] = ex;
-            ex += S.tot[lane * per + k];
+            base[lane * per + k] = ex;
+            ex += tot[lane * per + k];
         }
     }
     __syncthreads();
     for (int d = tid; d < nd; d += NT) {
-        int b = S.base[d];
+        int b = base[d];
         for (int w = 0; w < NW; w++) {
             int h = hist[w * 256 + d];
             hist[w * 256 + d] = b;
@@ -336,17 +354,19 @@ __device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* 
         }
     }
     if (modoff_out)
-        for (int d = tid; d <= M; d += NT) modoff_out[d] = d < M ? S.base[d] : n;
+        for (int d = tid; d <= M; d += NT) modoff_out[d] = d < M ? base[d] : n;
     __syncthreads();
     for (int b = beg; b < end; b += 32) {
         int j = b + lane;
         bool v = j < end;
-        unsigned d = v ? ((keys[src[j]] >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
+        uint32_t key = v ? ks[j] : 0u;
+        unsigned d = v ? ((key >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
         unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
         int pos = v ? hist[warp * 256 + d] + __popc(peers & lt) : 0;
         __syncwarp();
         if (v) {
-            dst[pos] = src[j];
+            kd[pos] = key;
+            id[pos] = is[j];
             if (lane == __ffs(peers) - 1) hist[warp * 256 + d] += __popc(peers);
         }
         __syncwarp();
@@ -354,39 +374,57 @@ __device__ void radix_pass(const uint32_t* keys, const uint16_t* src, uint16_t* 
     __syncthreads();
 }
 
-// Sort stage: keys, radix passes, gather.  Returns false (uniformly) when a
-// module id is out of range.
-template <int NT>
-__device__ bool sort_stage(const DevConfig& C, const Inputs& in, int off, int n, const Region& R,
-                           const Smem& S)
+// One block per event: phi16, stable sort by (module, phi16) in shared
+// memory, gather of the sorted hits.  Status SBT_ERR_ARG for a module id out
+// of range, SBT_ERR_CAPACITY above the configured hit limit.
+__global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, Sorted O)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    size_t okb, oia, oib, ohist, omisc;
+    sort_layout(C.nmax, &okb, &oia, &oib, &ohist, &omisc);
+    uint32_t* kA = (uint32_t*)smem_raw;
+    uint32_t* kB = (uint32_t*)(smem_raw + okb);
+    uint16_t* iA = (uint16_t*)(smem_raw + oia);
+    uint16_t* iB = (uint16_t*)(smem_raw + oib);
+    int* hist = (int*)(smem_raw + ohist);
+    int* tot = (int*)(smem_raw + omisc);
+    int* base = tot + 256;
+    int* misc = base + 256 + 40;
+    __shared__ int modoff[kMaxModules + 1];
     const int tid = threadIdx.x;
-    if (tid == 0) S.misc[kErr] = 0;
+    const int e = blockIdx.x;
+    const int off = in.offsets[e];
+    const int n = in.offsets[e + 1] - off;
+    if (n < 0 || n > C.nmax) {
+        if (tid == 0) O.status[e] = n < 0 ? SBT_ERR_ARG : SBT_ERR_CAPACITY;
+        return;
+    }
+    if (tid == 0) misc[kErr] = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += NT) {
+    for (int i = tid; i < n; i += kSortThreads) {
         int m = in.module[off + i];
         if (m < 0 || m >= C.M) {
-            S.misc[kErr] = SBT_ERR_ARG;
+            misc[kErr] = SBT_ERR_ARG;
             m = 0;
         }
-        R.keys[i] = ((uint32_t)m << 16) | phi16_of(in.x[off + i], in.y[off + i]);
-        R.idxA[i] = (uint16_t)i;
+        kA[i] = ((uint32_t)m << 16) | phi16_of(in.x[off + i], in.y[off + i]);
+        iA[i] = (uint16_t)i;
     }
     __syncthreads();
-    if (S.misc[kErr]) return false;
-    radix_pass<NT>(R.keys, R.idxA, R.idxB, n, 0, 8, S, nullptr, C.M);
-    radix_pass<NT>(R.keys, R.idxB, R.idxA, n, 8, 8, S, nullptr, C.M);
-    radix_pass<NT>(R.keys, R.idxA, R.idxB, n, 16, 6, S, S.modoff, C.M);
-    for (int p = tid; p < n; p += NT) {
-        int i = R.idxB[p];
-        R.phi[p] = (uint16_t)(R.keys[i] & 0xFFFFu);
-        R.coords[p] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
-        R.claim[p] = ~0ull;
-        R.idxA[p] = kNone;  // canonical-order marks
+    if (misc[kErr]) {
+        if (tid == 0) O.status[e] = SBT_ERR_ARG;
+        return;
     }
-    for (int w = tid; w < (n + 31) / 32; w += NT) S.flag[w] = 0u;
-    __syncthreads();
-    return true;
+    radix_pass(kA, iA, kB, iB, n, 0, 8, hist, tot, base, nullptr, C.M);
+    radix_pass(kB, iB, kA, iA, n, 8, 8, hist, tot, base, nullptr, C.M);
+    radix_pass(kA, iA, kB, iB, n, 16, 6, hist, tot, base, modoff, C.M);
+    for (int p = tid; p < n; p += kSortThreads) {
+        const int i = iB[p];
+        O.phi[off + p] = (uint16_t)(kB[p] & 0xFFFFu);
+        O.coords[off + p] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
+    }
+    for (int m = tid; m <= C.M; m += kSortThreads) O.modoff[(int64_t)e * (C.M + 1) + m] = modoff[m];
+    if (tid == 0) O.status[e] = SBT_OK;
 }
 
 // ------------------------------------------------------ seeding, following ---
@@ -630,7 +668,7 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S,
     int* misc = S.misc;
     const int cap = C.fcap > 0 ? min(C.fcap, forming_capacity(n)) : forming_capacity(n);
     const float sq_seed = sqrtf(C.S_seed), sq_follow = sqrtf(C.S_follow);
-    uint32_t* list = R.keys;  // free after the sort
+    uint32_t* list = R.list;
     if (tid == 0) {
         misc[kCnt0] = 0;
         misc[kCnt1] = 0;
@@ -651,6 +689,8 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S,
             misc[kCnt0 + nxt] = 0;
             misc[kNew] = 0;
         }
+        if (s + 3 <= M - 1)  // claim words of the target module start empty
+            for (int p = S.modoff[s + 3] + tid; p < S.modoff[s + 4]; p += NT) R.claim[p] = ~0ull;
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
         uint32_t* outer = list + (c1 - c0);
         for (int base = c0 + (tid & ~31); base < c1; base += NT) {
@@ -818,8 +858,8 @@ __device__ void output_stage(const DevConfig& C, int e, int off, int n, const Re
 {
     const int tid = threadIdx.x;
     const int T = S.misc[kNFin];
-    uint16_t* mark = R.idxA;
-    uint16_t* pos = R.idxB;
+    uint16_t* mark = R.mark;
+    uint16_t* pos = R.pos;
     for (int k = tid; k < T; k += NT) {
         uint32_t v = R.finals[k];
         int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
@@ -898,27 +938,28 @@ __device__ __forceinline__ void fail_event(int e, int code, const Staging& G, co
     }
 }
 
+// Search of one sorted event by the whole block.
 template <int NT>
-__device__ void run_event(const DevConfig& C, const Inputs& in, const Work& W, const Staging& G,
-                          const sbt_tracks& out, int e, int64_t hb, int64_t r, int cap,
-                          const Smem& S)
+__device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
+                          const Staging& G, const sbt_tracks& out, int e, int64_t hb, int64_t r,
+                          int cap, const Smem& S)
 {
+    const int tid = threadIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
-    if (n < 0) {
-        fail_event(e, SBT_ERR_ARG, G, out);
+    const int st = O.status[e];
+    if (st != SBT_OK || n > cap) {
+        fail_event(e, st != SBT_OK ? st : SBT_ERR_CAPACITY, G, out);
         return;
     }
-    if (n > C.nmax || n > cap) {
-        fail_event(e, SBT_ERR_CAPACITY, G, out);
-        return;
-    }
-    Region R = region_of(W, hb, r, cap);
-    if (!sort_stage<NT>(C, in, off, n, R, S)) {
-        fail_event(e, SBT_ERR_ARG, G, out);
-        __syncthreads();
-        return;
-    }
+    Region R = region_of(O, off, W, hb, r, cap);
+    for (int m = tid; m <= C.M; m += NT) S.modoff[m] = O.modoff[(int64_t)e * (C.M + 1) + m];
+    for (int w = tid; w < (n + 31) / 32; w += NT) S.flag[w] = 0u;
+    for (int p = tid; p < n; p += NT) R.mark[p] = kNone;
+    __syncthreads();
+    // claim words of the modules that are never a following target
+    for (int p = tid; p < S.modoff[min(3, C.M)]; p += NT) R.claim[p] = ~0ull;
+    __syncthreads();
     if (!search_stage<NT>(C, R, S, n)) {
         fail_event(e, SBT_ERR_CAPACITY, G, out);
         __syncthreads();
@@ -933,22 +974,22 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Work& W, c
 
 // One block per event.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_reco_plain(DevConfig C, Inputs in, Work W, Staging G,
-                                                    sbt_tracks out)
+__global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sorted O, Work W,
+                                                      Staging G, sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem S = carve(smem_raw, C.nmax, NT);
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
-    run_event<NT>(C, in, W, G, out, e, off, e, n, S);
+    run_event<NT>(C, in, O, W, G, out, e, off, e, max(n, 0), S);
 }
 
 // Persistent: each resident block takes events from the work queue in the
 // order of G.order (largest first) and reuses its own scratch region.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_reco_persistent(DevConfig C, Inputs in, Work W, Staging G,
-                                                         sbt_tracks out)
+__global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in, Sorted O, Work W,
+                                                           Staging G, sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem S = carve(smem_raw, C.nmax, NT);
@@ -959,7 +1000,7 @@ __global__ void __launch_bounds__(NT) k_reco_persistent(DevConfig C, Inputs in, 
         const int q = S.misc[kEvent];
         __syncthreads();
         if (q >= in.n_events) break;
-        run_event<NT>(C, in, W, G, out, G.order[q], hb, blockIdx.x, C.nmax, S);
+        run_event<NT>(C, in, O, W, G, out, G.order[q], hb, blockIdx.x, C.nmax, S);
     }
 }
 
@@ -1071,31 +1112,16 @@ __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Sta
     for (int j = lane; j < H; j += 32) dst[j] = src[j];
 }
 
-// Sort stage alone, for stage-level checks.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_debug_sort(DevConfig C, Inputs in, Work W, uint16_t* phi16,
-                                                    int32_t* perm, int32_t* modoff, int32_t* status)
+// Sort stage output copied out, for stage-level checks.
+__global__ void k_debug_sort_copy(DevConfig C, Inputs in, Sorted O, uint16_t* phi16, int32_t* perm,
+                                  int32_t* modoff)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, C.nmax, NT);
-    const int e = blockIdx.x;
-    const int off = in.offsets[e];
-    const int n = in.offsets[e + 1] - off;
-    if (n < 0 || n > C.nmax) {
-        if (threadIdx.x == 0) status[e] = SBT_ERR_CAPACITY;
-        return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < in.n_hits) {
+        phi16[i] = O.phi[i];
+        perm[i] = __float_as_int(O.coords[i].w);
     }
-    Region R = region_of(W, off, e, n);
-    if (!sort_stage<NT>(C, in, off, n, R, S)) {
-        if (threadIdx.x == 0) status[e] = SBT_ERR_ARG;
-        return;
-    }
-    for (int p = threadIdx.x; p < n; p += NT) {
-        phi16[off + p] = R.phi[p];
-        perm[off + p] = __float_as_int(R.coords[p].w);
-    }
-    for (int m = threadIdx.x; m <= C.M; m += NT) modoff[(int64_t)e * (C.M + 1) + m] = S.modoff[m];
-    if (threadIdx.x == 0) status[e] = SBT_OK;
+    if (i < (int64_t)in.n_events * (C.M + 1)) modoff[i] = O.modoff[i];
 }
 
 __global__ void k_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out)
@@ -1106,25 +1132,34 @@ __global__ void k_debug_phi16(const float* x, const float* y, int32_t n, uint16_
 
 // ------------------------------------------------------------ launchers ---
 
-template <int NT>
-static cudaError_t plain_nt(const DevConfig& C, const Inputs& in, const Work& W, const Staging& G,
-                            const sbt_tracks& out, cudaStream_t st)
+cudaError_t launch_sort(const DevConfig& C, const Inputs& in, const Sorted& O, cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_reco_plain<NT>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    size_t sm = sort_smem_bytes(C.nmax);
+    cudaError_t err = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    if (in.n_events > 0) k_reco_plain<NT><<<in.n_events, NT, sm, st>>>(C, in, W, G, out);
+    if (in.n_events > 0) k_sort<<<in.n_events, kSortThreads, sm, st>>>(C, in, O);
     return cudaGetLastError();
 }
 
-cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Work& W, const Staging& S,
-                         const sbt_tracks& out, int threads, cudaStream_t stream)
+template <int NT>
+static cudaError_t plain_nt(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
+                            const Staging& G, const sbt_tracks& out, cudaStream_t st)
+{
+    size_t sm = smem_bytes(C.nmax, NT);
+    cudaError_t err = cudaFuncSetAttribute(k_search_plain<NT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (in.n_events > 0) k_search_plain<NT><<<in.n_events, NT, sm, st>>>(C, in, O, W, G, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
+                         const Staging& S, const sbt_tracks& out, int threads, cudaStream_t stream)
 {
     switch (threads) {
-        case 64: return plain_nt<64>(C, in, W, S, out, stream);
-        case 128: return plain_nt<128>(C, in, W, S, out, stream);
-        case 256: return plain_nt<256>(C, in, W, S, out, stream);
+        case 64: return plain_nt<64>(C, in, O, W, S, out, stream);
+        case 128: return plain_nt<128>(C, in, O, W, S, out, stream);
+        case 256: return plain_nt<256>(C, in, O, W, S, out, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1139,11 +1174,11 @@ template <int NT>
 static int occupancy_nt(const DevConfig& C)
 {
     size_t sm = smem_bytes(C.nmax, NT);
-    if (cudaFuncSetAttribute(k_reco_persistent<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_search_persistent<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_reco_persistent<NT>, NT, sm) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_search_persistent<NT>, NT, sm) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -1160,26 +1195,26 @@ int persistent_blocks_per_sm(const DevConfig& C, int threads)
 }
 
 template <int NT>
-static cudaError_t persistent_nt(const DevConfig& C, const Inputs& in, const Work& W,
+static cudaError_t persistent_nt(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                                  const Staging& G, const sbt_tracks& out, int blocks,
                                  cudaStream_t st)
 {
     size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_reco_persistent<NT>,
+    cudaError_t err = cudaFuncSetAttribute(k_search_persistent<NT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    if (blocks > 0) k_reco_persistent<NT><<<blocks, NT, sm, st>>>(C, in, W, G, out);
+    if (blocks > 0) k_search_persistent<NT><<<blocks, NT, sm, st>>>(C, in, O, W, G, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Work& W,
+cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                               const Staging& S, const sbt_tracks& out, int threads, int blocks,
                               cudaStream_t stream)
 {
     switch (threads) {
-        case 64: return persistent_nt<64>(C, in, W, S, out, blocks, stream);
-        case 128: return persistent_nt<128>(C, in, W, S, out, blocks, stream);
-        case 256: return persistent_nt<256>(C, in, W, S, out, blocks, stream);
+        case 64: return persistent_nt<64>(C, in, O, W, S, out, blocks, stream);
+        case 128: return persistent_nt<128>(C, in, O, W, S, out, blocks, stream);
+        case 256: return persistent_nt<256>(C, in, O, W, S, out, blocks, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1209,31 +1244,15 @@ cudaError_t launch_finish(const DevConfig& C, const Inputs& in, const Staging& S
     return e;
 }
 
-int plain_kernel_count() { return 3; }
-
-template <int NT>
-static cudaError_t debug_sort_nt(const DevConfig& C, const Inputs& in, const Work& W, uint16_t* phi16,
-                                 int32_t* perm, int32_t* modoff, int32_t* status, cudaStream_t st)
+cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const Sorted& O,
+                                   uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
+                                   cudaStream_t stream)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_debug_sort<NT>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    if (in.n_events > 0)
-        k_debug_sort<NT><<<in.n_events, NT, sm, st>>>(C, in, W, phi16, perm, modoff, status);
+    const int64_t n = std::max<int64_t>(in.n_hits, (int64_t)in.n_events * (C.M + 1));
+    if (n > 0)
+        k_debug_sort_copy<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(C, in, O, phi16, perm,
+                                                                           module_offsets);
     return cudaGetLastError();
-}
-
-cudaError_t launch_debug_sort(const DevConfig& C, const Inputs& in, const Work& W,
-                              uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
-                              int32_t* status, int threads, cudaStream_t stream)
-{
-    switch (threads) {
-        case 64: return debug_sort_nt<64>(C, in, W, phi16, perm, module_offsets, status, stream);
-        case 128: return debug_sort_nt<128>(C, in, W, phi16, perm, module_offsets, status, stream);
-        case 256: return debug_sort_nt<256>(C, in, W, phi16, perm, module_offsets, status, stream);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out,

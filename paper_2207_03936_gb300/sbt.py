@@ -275,9 +275,9 @@ def sbt_autotune(h: Handle, x, y, z, module, event_offsets, stream=None) -> int:
 
 def sbt_profile_batched(h: Handle, x, y, z, module, event_offsets, out: TrackOutput, reps=3,
                         stream=None):
-    """Mean ms per launch of (ordering, persistent reconstruction, scan, consolidation)."""
+    """Mean ms per launch of (ordering, sort, persistent search, scan, consolidation)."""
     px, py, pz, pm, po, E, H = _inputs(x, y, z, module, event_offsets)
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 5)()
     oc = out.c_struct()
     _check(lib().sbt_profile_batched(h.h, px, py, pz, pm, po, E, H, ctypes.byref(oc), int(reps), ms,
                                      _stream(stream)), h.h)
