@@ -272,7 +272,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 
 // ------------------------------------------------------------- sorting ---
 
-constexpr int kSortThreads = 512;
+constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 
 // Shared memory of the sort kernel: keys and indices ping-pong (12 B per hit)
@@ -401,14 +401,30 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
     }
     if (tid == 0) misc[kErr] = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += kSortThreads) {
-        int m = in.module[off + i];
-        if (m < 0 || m >= C.M) {
-            misc[kErr] = SBT_ERR_ARG;
-            m = 0;
+    // keys: four hits per thread per round, loads issued before use
+    for (int i0 = tid; i0 < n; i0 += 4 * kSortThreads) {
+        float xs[4], ys[4];
+        int ms[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = i0 + u * kSortThreads;
+            const bool v = i < n;
+            xs[u] = v ? in.x[off + i] : 1.0f;
+            ys[u] = v ? in.y[off + i] : 0.0f;
+            ms[u] = v ? in.module[off + i] : 0;
         }
-        kA[i] = ((uint32_t)m << 16) | phi16_of(in.x[off + i], in.y[off + i]);
-        iA[i] = (uint16_t)i;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = i0 + u * kSortThreads;
+            if (i >= n) continue;
+            int m = ms[u];
+            if (m < 0 || m >= C.M) {
+                misc[kErr] = SBT_ERR_ARG;
+                m = 0;
+            }
+            kA[i] = ((uint32_t)m << 16) | phi16_of(xs[u], ys[u]);
+            iA[i] = (uint16_t)i;
+        }
     }
     __syncthreads();
     if (misc[kErr]) {
@@ -418,10 +434,25 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
     radix_pass(kA, iA, kB, iB, n, 0, 8, hist, tot, base, nullptr, C.M);
     radix_pass(kB, iB, kA, iA, n, 8, 8, hist, tot, base, nullptr, C.M);
     radix_pass(kA, iA, kB, iB, n, 16, 6, hist, tot, base, modoff, C.M);
-    for (int p = tid; p < n; p += kSortThreads) {
-        const int i = iB[p];
-        O.phi[off + p] = (uint16_t)(kB[p] & 0xFFFFu);
-        O.coords[off + p] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
+    // gather of the sorted hits, four per thread per round
+    for (int p0 = tid; p0 < n; p0 += 4 * kSortThreads) {
+        float4 c[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int p = p0 + u * kSortThreads;
+            if (p < n) {
+                const int i = iB[p];
+                c[u] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int p = p0 + u * kSortThreads;
+            if (p < n) {
+                O.phi[off + p] = (uint16_t)(kB[p] & 0xFFFFu);
+                O.coords[off + p] = c[u];
+            }
+        }
     }
     for (int m = tid; m <= C.M; m += kSortThreads) O.modoff[(int64_t)e * (C.M + 1) + m] = modoff[m];
     if (tid == 0) O.status[e] = SBT_OK;
