@@ -132,14 +132,16 @@ def serve(sbt, h, ev, rate_hz, budget_bytes, streams=4, max_batch=512, timeout=1
         t0 = time.perf_counter()
         srv.submit_schedule(ev, arrival)
         lat = []
-        while len(lat) < ev.n_events and time.perf_counter() - t0 < timeout:
-            for r in srv.poll(4096, timeout_s=0.01):
-                lat.append(r.latency_s)
+        n_done = 0
+        while n_done < ev.n_events and time.perf_counter() - t0 < timeout:
+            _, _, l = srv.drain(65536, timeout_s=0.01)
+            lat.append(l)
+            n_done += len(l)
         span = time.perf_counter() - t0
+        lat = np.concatenate(lat) if lat else np.zeros(0)
         st = srv.stats()
     finally:
         srv.close()
-    lat = np.array(lat)
     return {"offered_hz": rate_hz, "events": int(len(lat)), "value": len(lat) / span,
             "unit": "events/s", "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,

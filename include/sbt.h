@@ -141,10 +141,12 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
 
 /*
  * End-to-end form for callers holding host memory: copies the inputs (host)
- * to the device, runs the batched reconstruction and copies the tracks back
- * into host arrays of the sbt_tracks layout (out_host pointers are host
- * memory; counts is host too).  Synchronous: returns when the host arrays are
- * filled.  Pinned host memory gives full copy bandwidth.
+ * to the device, reconstructs with the batched kernels and copies the tracks
+ * back into host arrays of the sbt_tracks layout (out_host pointers are host
+ * memory; counts is host too).  The batch is processed in chunks of whole
+ * events so that uploads, kernels and downloads of different chunks overlap.
+ * Synchronous: returns when the host arrays are filled.  Pinned host memory
+ * gives full copy bandwidth and true overlap.
  */
 sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, const float* z,
                                 const int32_t* module, const int32_t* event_offsets,
@@ -272,7 +274,9 @@ sbt_status sbt_server_submit(sbt_server* s, int64_t request_id, const float* x, 
 /* Open-loop load generator: a native thread submits event e of the host batch
  * (x, y, z, module [event_offsets[e] .. event_offsets[e+1])) arrival_s[e]
  * seconds after this call, with request id first_id + e.  The call copies the
- * batch and returns at once; results arrive through sbt_server_poll. */
+ * batch into pinned host memory (uploads of consecutive events then need no
+ * further copy) and returns at once; results arrive through
+ * sbt_server_poll or sbt_server_drain. */
 sbt_status sbt_server_submit_schedule(sbt_server* s, const float* x, const float* y,
                                       const float* z, const int32_t* module,
                                       const int32_t* event_offsets, int32_t n_events,
@@ -283,6 +287,13 @@ sbt_status sbt_server_submit_schedule(sbt_server* s, const float* x, const float
  * returns SBT_ERR_TIMEOUT when none finished in time. */
 sbt_status sbt_server_poll(sbt_server* s, sbt_result* results, int32_t max_results,
                            int32_t* n_out, double timeout_s);
+
+/* For consumers that only need completions: up to max_results finished
+ * requests as (ids, status, latency_s) host arrays; their results are freed
+ * at once.  Waits at most timeout_s for the first (0 = do not wait); returns
+ * SBT_ERR_TIMEOUT when none finished in time. */
+sbt_status sbt_server_drain(sbt_server* s, int64_t* ids, int32_t* status, double* latency_s,
+                            int32_t max_results, int32_t* n_out, double timeout_s);
 
 /* Frees the host memory of a polled result. */
 sbt_status sbt_server_release(sbt_server* s, int64_t request_id);

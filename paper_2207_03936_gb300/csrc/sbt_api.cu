@@ -18,6 +18,10 @@ namespace {
 
 std::string g_create_error;
 
+// Host pipeline: events per chunk and the most chunks per call.
+constexpr int64_t kChunkEvents = 12500;
+constexpr int kMaxChunks = 16;
+
 // One device allocation carved into aligned sub-arrays.
 struct Arena {
     void* base = nullptr;
@@ -132,6 +136,8 @@ struct sbt_handle {
     Arena plain_arena, pers_arena, stage_arena, host_arena, misc_arena, sorted_arena;
     int tuned_threads = 0;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    int32_t* host_counts = nullptr;  // pinned, 4 per chunk of the host pipeline
     cudaGraphExec_t exec = nullptr;
     GraphKey key{};
     bool have_key = false;
@@ -331,6 +337,9 @@ sbt_status sbt_destroy(sbt_handle* h)
     cudaDeviceSynchronize();
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->copy_in) cudaStreamDestroy(h->copy_in);
+    if (h->copy_out) cudaStreamDestroy(h->copy_out);
+    if (h->host_counts) cudaFreeHost(h->host_counts);
     h->plain_arena.release();
     h->sorted_arena.release();
     h->pers_arena.release();
@@ -444,72 +453,153 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, oh);
     if (st != SBT_OK || !oh) return st != SBT_OK ? st : SBT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    // device copies of the inputs and full-capacity outputs
+    cudaError_t e = cudaSuccess;
+    if (!h->copy_in) e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->copy_out) e = cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->host_counts) e = cudaMallocHost(&h->host_counts, sizeof(int32_t) * 4 * kMaxChunks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline set-up");
+    // chunks of whole events: inputs of chunk c+1 upload while chunk c
+    // computes, results of chunk c download while chunk c+1 computes
     const int64_t H = n_hits, E = n_events;
-    const int64_t capT = H / 3 + 1, capH = H + 1;
-    Carver c0(nullptr);
-    auto layout = [&](Carver& c, float** dx, float** dy, float** dz, int32_t** dm, int32_t** doff,
-                      sbt_tracks* d) {
-        *dx = c.take<float>(H);
-        *dy = c.take<float>(H);
-        *dz = c.take<float>(H);
-        *dm = c.take<int32_t>(H);
-        *doff = c.take<int32_t>(E + 1);
-        d->track_offsets = c.take<int32_t>(E + 1);
-        d->hit_offsets = c.take<int32_t>(capT + 1);
-        d->track_hits = c.take<int32_t>(capH);
-        d->params = c.take<float>(4 * capT);
-        d->chi2 = c.take<float>(capT);
-        d->ndof = c.take<int32_t>(capT);
-        d->event_status = c.take<int32_t>(E);
-        d->counts = c.take<int32_t>(4);
-        d->cap_tracks = (int32_t)capT;
-        d->cap_hits = (int32_t)capH;
+    const int C = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, (E + kChunkEvents - 1) / kChunkEvents));
+    std::vector<int32_t> e0(C + 1);
+    for (int c = 0; c <= C; c++) e0[c] = (int32_t)((E * c) / C);
+    auto layout = [&](Carver& cv, float** dx, float** dy, float** dz, int32_t** dm, int32_t** doff,
+                      int32_t** dto, int32_t** dho, int32_t** dth, float** dpar, float** dchi,
+                      int32_t** dndof, int32_t** dstat, int32_t** dcnt, int64_t** drun) {
+        *dx = cv.take<float>(H);
+        *dy = cv.take<float>(H);
+        *dz = cv.take<float>(H);
+        *dm = cv.take<int32_t>(H);
+        *doff = cv.take<int32_t>(E + 1);
+        *dto = cv.take<int32_t>(E + C);
+        *dho = cv.take<int32_t>(H / 3 + 2 * C + 1);
+        *dth = cv.take<int32_t>(H + C);
+        *dpar = cv.take<float>(4 * (H / 3 + 2 * C));
+        *dchi = cv.take<float>(H / 3 + 2 * C);
+        *dndof = cv.take<int32_t>(H / 3 + 2 * C);
+        *dstat = cv.take<int32_t>(E);
+        *dcnt = cv.take<int32_t>(4 * C);
+        *drun = cv.take<int64_t>(2);
     };
-    float *dx, *dy, *dz;
-    int32_t *dm, *doff;
-    sbt_tracks d;
-    layout(c0, &dx, &dy, &dz, &dm, &doff, &d);
-    cudaError_t e = h->host_arena.reserve(c0.off + 256);
+    float *dx, *dy, *dz, *dpar, *dchi;
+    int32_t *dm, *doff, *dto, *dho, *dth, *dndof, *dstat, *dcnt;
+    int64_t* drun;
+    Carver c0(nullptr);
+    layout(c0, &dx, &dy, &dz, &dm, &doff, &dto, &dho, &dth, &dpar, &dchi, &dndof, &dstat, &dcnt, &drun);
+    e = h->host_arena.reserve(c0.off + 256);
     if (e != cudaSuccess) return cuda_fail(h, e, "host-path allocation");
     Carver c1(h->host_arena.base);
-    layout(c1, &dx, &dy, &dz, &dm, &doff, &d);
-    e = cudaMemcpyAsync(dx, x, sizeof(float) * H, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, sizeof(float) * H, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z, sizeof(float) * H, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dm, module, sizeof(int32_t) * H, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(doff, event_offsets, sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
-    st = sbt_reconstruct_batched(h, dx, dy, dz, dm, doff, n_events, n_hits, &d, stream);
-    if (st != SBT_OK) return st;
-    int32_t counts[4];
-    e = cudaMemcpyAsync(counts, d.counts, sizeof(counts), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "count copy");
-    const int64_t T = counts[0], HH = counts[1];
-    std::memcpy(oh->counts, counts, sizeof(counts));
-    if (T > oh->cap_tracks || HH > oh->cap_hits) oh->counts[2] = SBT_ERR_CAPACITY;
-    e = cudaMemcpyAsync(oh->track_offsets, d.track_offsets, sizeof(int32_t) * (E + 1),
-                        cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(oh->event_status, d.event_status, sizeof(int32_t) * E,
-                            cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && oh->counts[2] == SBT_OK) {
-        e = cudaMemcpyAsync(oh->hit_offsets, d.hit_offsets, sizeof(int32_t) * (T + 1),
-                            cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && HH > 0)
-            e = cudaMemcpyAsync(oh->track_hits, d.track_hits, sizeof(int32_t) * HH,
-                                cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && T > 0)
-            e = cudaMemcpyAsync(oh->params, d.params, sizeof(float) * 4 * T, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && T > 0)
-            e = cudaMemcpyAsync(oh->chi2, d.chi2, sizeof(float) * T, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && T > 0)
-            e = cudaMemcpyAsync(oh->ndof, d.ndof, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s);
+    layout(c1, &dx, &dy, &dz, &dm, &doff, &dto, &dho, &dth, &dpar, &dchi, &dndof, &dstat, &dcnt, &drun);
+    const int threads = default_threads(h, true);
+    const int blocks = persistent_blocks(h, threads);
+    Staging S;
+    Work W;
+    Sorted O;
+    if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
+    if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) return st;
+    if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
+    std::vector<cudaEvent_t> in_ev(C), comp_ev(C);
+    for (int c = 0; c < C; c++) {
+        cudaEventCreateWithFlags(&in_ev[c], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&comp_ev[c], cudaEventDisableTiming);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "output copy");
+    auto cleanup = [&]() {
+        for (int c = 0; c < C; c++) {
+            cudaEventDestroy(in_ev[c]);
+            cudaEventDestroy(comp_ev[c]);
+        }
+    };
+    // uploads
+    e = cudaMemcpyAsync(doff, event_offsets, sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice, h->copy_in);
+    for (int c = 0; c < C && e == cudaSuccess; c++) {
+        const int64_t a = event_offsets[e0[c]], b = event_offsets[e0[c + 1]];
+        const size_t nb = sizeof(float) * (size_t)(b - a);
+        if (nb) {
+            e = cudaMemcpyAsync(dx + a, x + a, nb, cudaMemcpyHostToDevice, h->copy_in);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dy + a, y + a, nb, cudaMemcpyHostToDevice, h->copy_in);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dz + a, z + a, nb, cudaMemcpyHostToDevice, h->copy_in);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dm + a, module + a, nb, cudaMemcpyHostToDevice, h->copy_in);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(in_ev[c], h->copy_in);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(drun, 0, 2 * sizeof(int64_t), s);
+    // per-chunk reconstruction; chunk c's outputs start at event e0[c] + c,
+    // track slot hits/3 + 2c and hit slot hits + c of the device buffers
+    std::vector<sbt_tracks> dc(C);
+    for (int c = 0; c < C && e == cudaSuccess; c++) {
+        const int32_t Ec = e0[c + 1] - e0[c];
+        const int64_t a = event_offsets[e0[c]], b = event_offsets[e0[c + 1]];
+        sbt_tracks& d = dc[c];
+        const int64_t tslot = a / 3 + 2 * c;
+        d.track_offsets = dto + e0[c] + c;
+        d.hit_offsets = dho + tslot;
+        d.track_hits = dth + a + c;
+        d.params = dpar + 4 * tslot;
+        d.chi2 = dchi + tslot;
+        d.ndof = dndof + tslot;
+        d.event_status = dstat + e0[c];
+        d.counts = dcnt + 4 * c;
+        d.cap_tracks = (int32_t)((b - a) / 3 + 1);
+        d.cap_hits = (int32_t)(b - a + 1);
+        e = cudaStreamWaitEvent(s, in_ev[c], 0);
+        Inputs in = make_inputs(dx, dy, dz, dm, doff + e0[c], Ec, (int32_t)b);
+        if (e == cudaSuccess) {
+            st = enqueue_batched(h, in, O, S, W, d, threads, blocks, s);
+            if (st != SBT_OK) {
+                cleanup();
+                return st;
+            }
+        }
+        if (e == cudaSuccess) e = launch_offset_fixup(d.track_offsets, Ec, d.hit_offsets, d.counts, drun, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->host_counts + 4 * c, d.counts, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(comp_ev[c], s);
+    }
+    // downloads as chunks finish
+    int64_t T = 0, HH = 0, failed = 0;
+    bool cap_ok = true;
+    for (int c = 0; c < C && e == cudaSuccess; c++) {
+        e = cudaEventSynchronize(comp_ev[c]);
+        if (e != cudaSuccess) break;
+        const int32_t* cn = h->host_counts + 4 * c;
+        const int32_t Ec = e0[c + 1] - e0[c];
+        const int64_t Tc = cn[0], Hc = cn[1];
+        failed += cn[3];
+        const sbt_tracks& d = dc[c];
+        cudaStream_t o = h->copy_out;
+        e = cudaMemcpyAsync(oh->track_offsets + e0[c], d.track_offsets, sizeof(int32_t) * (Ec + (c == C - 1)),
+                            cudaMemcpyDeviceToHost, o);
+        if (e == cudaSuccess && Ec)
+            e = cudaMemcpyAsync(oh->event_status + e0[c], d.event_status, sizeof(int32_t) * Ec,
+                                cudaMemcpyDeviceToHost, o);
+        if (cn[2] != SBT_OK || T + Tc > oh->cap_tracks || HH + Hc > oh->cap_hits) cap_ok = false;
+        if (e == cudaSuccess && cap_ok) {
+            e = cudaMemcpyAsync(oh->hit_offsets + T, d.hit_offsets, sizeof(int32_t) * (Tc + 1),
+                                cudaMemcpyDeviceToHost, o);
+            if (e == cudaSuccess && Hc)
+                e = cudaMemcpyAsync(oh->track_hits + HH, d.track_hits, sizeof(int32_t) * Hc,
+                                    cudaMemcpyDeviceToHost, o);
+            if (e == cudaSuccess && Tc) {
+                e = cudaMemcpyAsync(oh->params + 4 * T, d.params, 16 * Tc, cudaMemcpyDeviceToHost, o);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(oh->chi2 + T, d.chi2, 4 * Tc, cudaMemcpyDeviceToHost, o);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(oh->ndof + T, d.ndof, 4 * Tc, cudaMemcpyDeviceToHost, o);
+            }
+        }
+        T += Tc;
+        HH += Hc;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_out);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline");
+    if (E == 0) oh->track_offsets[0] = 0;
+    oh->counts[0] = (int32_t)T;
+    oh->counts[1] = (int32_t)HH;
+    oh->counts[2] = cap_ok ? SBT_OK : SBT_ERR_CAPACITY;
+    oh->counts[3] = (int32_t)failed;
+    h->launches_last = C * 6;
     return SBT_OK;
 }
 

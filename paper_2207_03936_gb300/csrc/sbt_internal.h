@@ -115,6 +115,8 @@ cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const S
                                    cudaStream_t stream);
 cudaError_t launch_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out,
                                cudaStream_t stream);
+cudaError_t launch_offset_fixup(int32_t* track_offsets, int32_t n_events, int32_t* hit_offsets,
+                                const int32_t* counts, int64_t* running, cudaStream_t stream);
 int persistent_blocks_per_sm(const DevConfig& C, int threads);
 
 // Adjoint (sbt_adjoint.cu).

@@ -1143,6 +1143,26 @@ __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Sta
     for (int j = lane; j < H; j += 32) dst[j] = src[j];
 }
 
+// Chunked host pipeline: adds the totals of the earlier chunks to one chunk's
+// CSR offsets (track_offsets [n_events + 1], hit_offsets [counts[0] + 1]) and
+// advances the running totals (running[0] tracks, running[1] hits).
+__global__ void __launch_bounds__(1024) k_offset_fixup(int32_t* track_offsets, int32_t n_events,
+                                                       int32_t* hit_offsets, const int32_t* counts,
+                                                       int64_t* running)
+{
+    const int64_t bt = running[0], bh = running[1];
+    const int T = counts[0];
+    const bool ok = counts[2] == SBT_OK;
+    for (int i = threadIdx.x; i <= n_events; i += 1024) track_offsets[i] += (int32_t)bt;
+    if (ok)
+        for (int t = threadIdx.x; t <= T; t += 1024) hit_offsets[t] += (int32_t)bh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        running[0] = bt + T;
+        running[1] = bh + counts[1];
+    }
+}
+
 // Sort stage output copied out, for stage-level checks.
 __global__ void k_debug_sort_copy(DevConfig C, Inputs in, Sorted O, uint16_t* phi16, int32_t* perm,
                                   int32_t* modoff)
@@ -1283,6 +1303,13 @@ cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const S
     if (n > 0)
         k_debug_sort_copy<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(C, in, O, phi16, perm,
                                                                            module_offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offset_fixup(int32_t* track_offsets, int32_t n_events, int32_t* hit_offsets,
+                                const int32_t* counts, int64_t* running, cudaStream_t stream)
+{
+    k_offset_fixup<<<1, 1024, 0, stream>>>(track_offsets, n_events, hit_offsets, counts, running);
     return cudaGetLastError();
 }
 

@@ -34,11 +34,32 @@ double now_s()
     return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
 }
 
+// One event to reconstruct.  Its hits either live in the request's own
+// vectors (sbt_server_submit) or in a pinned batch owned by the open-loop
+// feeder (sbt_server_submit_schedule), kept alive by `hold`.
 struct Request {
     int64_t id = 0;
-    std::vector<float> x, y, z;
-    std::vector<int32_t> m;
+    std::vector<float> ox, oy, oz;
+    std::vector<int32_t> om;
+    const float *x = nullptr, *y = nullptr, *z = nullptr;
+    const int32_t* m = nullptr;
+    int32_t n = 0;
+    bool pinned = false;
+    std::shared_ptr<void> hold;
     double t_submit = 0.0;
+};
+
+// Pinned copy of a scheduled batch.
+struct PinnedBatch {
+    float *x = nullptr, *y = nullptr, *z = nullptr;
+    int32_t* m = nullptr;
+    ~PinnedBatch()
+    {
+        if (x) cudaFreeHost(x);
+        if (y) cudaFreeHost(y);
+        if (z) cudaFreeHost(z);
+        if (m) cudaFreeHost(m);
+    }
 };
 
 struct Finished {
@@ -148,7 +169,7 @@ void finish_batch(sbt_server* S, Slot& sl, double t_done)
         Finished f;
         f.id = sl.reqs[k].id;
         f.latency = t_done - sl.reqs[k].t_submit;
-        const int32_t n = (int32_t)sl.reqs[k].x.size();
+        const int32_t n = sl.reqs[k].n;
         if (sl.failed) {
             f.status = SBT_ERR_CUDA;
             f.hit_offsets.assign(1, 0);
@@ -184,17 +205,27 @@ bool launch_batch(sbt_server* S, Slot& sl)
 {
     const int32_t E = (int32_t)sl.reqs.size();
     int64_t H64 = 0;
-    for (auto& r : sl.reqs) H64 += (int64_t)r.x.size();
+    for (auto& r : sl.reqs) H64 += (int64_t)r.n;
     const int32_t H = (int32_t)H64;
     const size_t capT = (size_t)H / 3 + 1, capH = (size_t)H + 1;
     cudaError_t e = cudaSuccess;
     auto need = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
     };
-    need(sl.hx.reserve(H)); need(sl.hy.reserve(H)); need(sl.hz.reserve(H)); need(sl.hm.reserve(H));
+    // a group of scheduled events that are consecutive in one pinned batch is
+    // uploaded directly; anything else is packed into the slot's staging
+    bool direct = sl.reqs[0].pinned;
+    for (int32_t k = 1; k < E && direct; k++) {
+        const Request& p = sl.reqs[k - 1];
+        const Request& r = sl.reqs[k];
+        direct = r.pinned && r.x == p.x + p.n && r.y == p.y + p.n && r.z == p.z + p.n && r.m == p.m + p.n;
+    }
     need(sl.hoff.reserve(E + 1)); need(sl.hto.reserve(E + 1)); need(sl.hho.reserve(capT + 1));
     need(sl.hth.reserve(capH)); need(sl.hparams.reserve(4 * capT)); need(sl.hchi2.reserve(capT));
     need(sl.hstat.reserve(E)); need(sl.hcounts.reserve(4));
+    if (!direct) {
+        need(sl.hx.reserve(H)); need(sl.hy.reserve(H)); need(sl.hz.reserve(H)); need(sl.hm.reserve(H));
+    }
     need(sl.dx.reserve(H)); need(sl.dy.reserve(H)); need(sl.dz.reserve(H)); need(sl.dm.reserve(H));
     need(sl.doff.reserve(E + 1)); need(sl.dto.reserve(E + 1)); need(sl.dho.reserve(capT + 1));
     need(sl.dth.reserve(capH)); need(sl.dparams.reserve(4 * capT)); need(sl.dchi2.reserve(capT));
@@ -203,20 +234,28 @@ bool launch_batch(sbt_server* S, Slot& sl)
     int32_t o = 0;
     for (int32_t k = 0; k < E; k++) {
         const Request& r = sl.reqs[k];
-        const size_t n = r.x.size();
+        const size_t n = (size_t)r.n;
         sl.hoff.p[k] = o;
-        std::memcpy(sl.hx.p + o, r.x.data(), 4 * n);
-        std::memcpy(sl.hy.p + o, r.y.data(), 4 * n);
-        std::memcpy(sl.hz.p + o, r.z.data(), 4 * n);
-        std::memcpy(sl.hm.p + o, r.m.data(), 4 * n);
+        if (!direct && n) {
+            std::memcpy(sl.hx.p + o, r.x, 4 * n);
+            std::memcpy(sl.hy.p + o, r.y, 4 * n);
+            std::memcpy(sl.hz.p + o, r.z, 4 * n);
+            std::memcpy(sl.hm.p + o, r.m, 4 * n);
+        }
         o += (int32_t)n;
     }
     sl.hoff.p[E] = o;
     cudaStream_t s = sl.stream;
-    need(cudaMemcpyAsync(sl.dx.p, sl.hx.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
-    need(cudaMemcpyAsync(sl.dy.p, sl.hy.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
-    need(cudaMemcpyAsync(sl.dz.p, sl.hz.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
-    need(cudaMemcpyAsync(sl.dm.p, sl.hm.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+    const float* sx = direct ? sl.reqs[0].x : sl.hx.p;
+    const float* sy = direct ? sl.reqs[0].y : sl.hy.p;
+    const float* sz = direct ? sl.reqs[0].z : sl.hz.p;
+    const int32_t* sm = direct ? sl.reqs[0].m : sl.hm.p;
+    if (H) {
+        need(cudaMemcpyAsync(sl.dx.p, sx, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dy.p, sy, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dz.p, sz, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dm.p, sm, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+    }
     need(cudaMemcpyAsync(sl.doff.p, sl.hoff.p, 4 * (size_t)(E + 1), cudaMemcpyHostToDevice, s));
     if (e != cudaSuccess) return false;
     sbt_tracks out;
@@ -266,10 +305,10 @@ void worker_loop(sbt_server* S)
                 std::lock_guard<std::mutex> lk(S->mu);
                 while (!S->pending.empty() && (int32_t)take.size() < S->max_batch) {
                     const Request& r = S->pending.front();
-                    int64_t b = batch_bytes(hits + (int64_t)r.x.size(), (int64_t)take.size() + 1);
+                    int64_t b = batch_bytes(hits + (int64_t)r.n, (int64_t)take.size() + 1);
                     if (S->in_flight_bytes + b > S->budget && !take.empty()) break;
                     if (S->in_flight_bytes + b > S->budget && S->in_flight_bytes > 0) break;
-                    hits += (int64_t)r.x.size();
+                    hits += (int64_t)r.n;
                     bytes = b;
                     take.push_back(std::move(S->pending.front()));
                     S->pending.pop_front();
@@ -369,10 +408,15 @@ sbt_status sbt_server_submit(sbt_server* S, int64_t request_id, const float* x, 
     if (S->stop.load()) return SBT_ERR_STATE;
     Request r;
     r.id = request_id;
-    r.x.assign(x, x + n);
-    r.y.assign(y, y + n);
-    r.z.assign(z, z + n);
-    r.m.assign(module, module + n);
+    r.ox.assign(x, x + n);
+    r.oy.assign(y, y + n);
+    r.oz.assign(z, z + n);
+    r.om.assign(module, module + n);
+    r.x = r.ox.data();
+    r.y = r.oy.data();
+    r.z = r.oz.data();
+    r.m = r.om.data();
+    r.n = n;
     r.t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -395,26 +439,88 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
     if (!S || n_events < 0 || !event_offsets || !arrival_s) return SBT_ERR_ARG;
     if (S->feeder.joinable()) S->feeder.join();
     const int32_t H = event_offsets[n_events];
-    std::vector<float> vx(x, x + H), vy(y, y + H), vz(z, z + H);
-    std::vector<int32_t> vm(module, module + H), vo(event_offsets, event_offsets + n_events + 1);
+    auto batch = std::make_shared<PinnedBatch>();
+    const size_t nb = sizeof(float) * (size_t)std::max(H, 1);
+    if (cudaMallocHost(&batch->x, nb) != cudaSuccess || cudaMallocHost(&batch->y, nb) != cudaSuccess ||
+        cudaMallocHost(&batch->z, nb) != cudaSuccess || cudaMallocHost(&batch->m, nb) != cudaSuccess)
+        return SBT_ERR_CUDA;
+    if (H) {
+        std::memcpy(batch->x, x, sizeof(float) * H);
+        std::memcpy(batch->y, y, sizeof(float) * H);
+        std::memcpy(batch->z, z, sizeof(float) * H);
+        std::memcpy(batch->m, module, sizeof(int32_t) * H);
+    }
+    std::vector<int32_t> vo(event_offsets, event_offsets + n_events + 1);
     std::vector<double> at(arrival_s, arrival_s + n_events);
-    S->feeder = std::thread([S, vx = std::move(vx), vy = std::move(vy), vz = std::move(vz),
-                             vm = std::move(vm), vo = std::move(vo), at = std::move(at), first_id,
-                             n_events]() {
+    S->feeder = std::thread([S, batch, vo = std::move(vo), at = std::move(at), first_id, n_events]() {
         const auto t0 = Clock::now();
-        for (int32_t e = 0; e < n_events && !S->stop.load(); e++) {
+        int32_t e = 0;
+        while (e < n_events && !S->stop.load()) {
             const auto due = t0 + std::chrono::duration_cast<Clock::duration>(
                                       std::chrono::duration<double>(at[e]));
-            while (Clock::now() < due) {
-                auto left = due - Clock::now();
+            auto now = Clock::now();
+            if (now < due) {
+                auto left = due - now;
                 if (left > std::chrono::microseconds(200))
                     std::this_thread::sleep_for(left - std::chrono::microseconds(100));
+                continue;
             }
-            const int32_t lo = vo[e], n = vo[e + 1] - vo[e];
-            sbt_server_submit(S, first_id + e, vx.data() + lo, vy.data() + lo, vz.data() + lo,
-                              vm.data() + lo, n);
+            // submit every event that is due
+            std::vector<Request> due_reqs;
+            const double ts = now_s();
+            while (e < n_events && t0 + std::chrono::duration_cast<Clock::duration>(
+                                          std::chrono::duration<double>(at[e])) <= now) {
+                Request r;
+                r.id = first_id + e;
+                const int32_t lo = vo[e];
+                r.x = batch->x + lo;
+                r.y = batch->y + lo;
+                r.z = batch->z + lo;
+                r.m = batch->m + lo;
+                r.n = vo[e + 1] - lo;
+                r.pinned = true;
+                r.hold = batch;
+                r.t_submit = ts;
+                due_reqs.push_back(std::move(r));
+                e++;
+            }
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (auto& r : due_reqs) S->pending.push_back(std::move(r));
+                S->st_submitted += (double)due_reqs.size();
+            }
+            S->cv_work.notify_one();
         }
     });
+    return SBT_OK;
+}
+
+/*
+ * Finished requests for consumers that only need their completion: up to
+ * max_results (request id, status, latency) triples; the results are released
+ * at once.  Waits at most timeout_s for the first one.
+ */
+sbt_status sbt_server_drain(sbt_server* S, int64_t* ids, int32_t* status, double* latency_s,
+                            int32_t max_results, int32_t* n_out, double timeout_s)
+{
+    if (!S || !n_out || max_results < 0 || (max_results > 0 && (!ids || !status || !latency_s)))
+        return SBT_ERR_ARG;
+    *n_out = 0;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->finished.empty() && timeout_s > 0)
+        S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                            [&] { return !S->finished.empty(); });
+    if (S->finished.empty()) return timeout_s > 0 ? SBT_ERR_TIMEOUT : SBT_OK;
+    int32_t k = 0;
+    while (k < max_results && !S->finished.empty()) {
+        const Finished& f = S->finished.front();
+        ids[k] = f.id;
+        status[k] = f.status;
+        latency_s[k] = f.latency;
+        S->finished.pop_front();
+        k++;
+    }
+    *n_out = k;
     return SBT_OK;
 }
 

@@ -353,6 +353,7 @@ def _server_sigs():
         "sbt_server_submit": (_I32, [_P, _I64, _P, _P, _P, _P, _I32]),
         "sbt_server_submit_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _P, _I64]),
         "sbt_server_poll": (_I32, [_P, _P, _I32, _P, ctypes.c_double]),
+        "sbt_server_drain": (_I32, [_P, _P, _P, _P, _I32, _P, ctypes.c_double]),
         "sbt_server_release": (_I32, [_P, _I64]),
         "sbt_server_stats": (_I32, [_P, _P]),
         "sbt_server_inject_failure": (_I32, [_P]),
@@ -424,6 +425,22 @@ class Server:
             out.append(ServedResult(r.request_id, r.status, ho, th, pr.reshape(T, 4), c2, r.latency_s))
             self.L.sbt_server_release(self.s, r.request_id)
         return out
+
+    def drain(self, max_results: int = 65536, timeout_s: float = 0.0):
+        """(ids, status, latency_s) numpy arrays of finished requests; results released."""
+        import numpy as np
+        ids = np.empty(max_results, np.int64)
+        st = np.empty(max_results, np.int32)
+        lat = np.empty(max_results, np.float64)
+        n = ctypes.c_int32()
+        rc = self.L.sbt_server_drain(self.s, ids.ctypes.data, st.ctypes.data, lat.ctypes.data,
+                                     max_results, ctypes.byref(n), float(timeout_s))
+        if rc == SBT_ERR_TIMEOUT:
+            n.value = 0
+        else:
+            _check(rc)
+        k = n.value
+        return ids[:k], st[:k], lat[:k]
 
     def stats(self) -> dict:
         v = (ctypes.c_double * 8)()
