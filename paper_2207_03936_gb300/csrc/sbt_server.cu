@@ -1,13 +1,16 @@
 // Continuous-batching request loop.
 //
-// A background host thread repeatedly (1) harvests finished batches (CUDA
-// event queries; no blocking synchronisation), (2) admits pending events in
-// arrival order while a free stream slot exists and the device-memory budget
-// allows, packing them into one batch: pinned staging copy, H2D on the slot's
-// stream, reconstruction on the slot's own handle, D2H of the results and an
-// event record.  Several slots are in flight at once, so events that arrive
-// while others run on the GPU are admitted and overlap them.  No device-side
-// wait exists anywhere: the GPU never spins on host state.
+// Two host threads share a set of stream slots:
+//   - the launcher admits pending events in arrival order while a slot is
+//     free and the device-memory budget allows, and enqueues the group on the
+//     slot's stream: upload (straight from the submitter's pinned batch when
+//     the events are consecutive in it), reconstruction on the slot's own
+//     handle, download of the results into a pinned result block, event record;
+//   - the harvester watches the slots' events and publishes finished requests
+//     (no copies: a request refers to its batch's result block).
+// Several slots are in flight at once, so events arriving while others run on
+// the GPU are admitted as soon as a slot and memory free up, and their work
+// overlaps on the device.  No device code ever waits on host state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,48 +35,6 @@ using Clock = std::chrono::steady_clock;
 double now_s()
 {
     return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
-}
-
-// One event to reconstruct.  Its hits either live in the request's own
-// vectors (sbt_server_submit) or in a pinned batch owned by the open-loop
-// feeder (sbt_server_submit_schedule), kept alive by `hold`.
-struct Request {
-    int64_t id = 0;
-    std::vector<float> ox, oy, oz;
-    std::vector<int32_t> om;
-    const float *x = nullptr, *y = nullptr, *z = nullptr;
-    const int32_t* m = nullptr;
-    int32_t n = 0;
-    bool pinned = false;
-    std::shared_ptr<void> hold;
-    double t_submit = 0.0;
-};
-
-// Pinned copy of a scheduled batch.
-struct PinnedBatch {
-    float *x = nullptr, *y = nullptr, *z = nullptr;
-    int32_t* m = nullptr;
-    ~PinnedBatch()
-    {
-        if (x) cudaFreeHost(x);
-        if (y) cudaFreeHost(y);
-        if (z) cudaFreeHost(z);
-        if (m) cudaFreeHost(m);
-    }
-};
-
-struct Finished {
-    int64_t id = 0;
-    int32_t status = 0;
-    std::vector<int32_t> hit_offsets, track_hits;
-    std::vector<float> params, chi2;
-    double latency = 0.0;
-};
-
-// Device bytes one batch needs (inputs, outputs and the plain workspace).
-int64_t batch_bytes(int64_t hits, int64_t events)
-{
-    return hits * 96 + events * 64 + (1 << 16);
 }
 
 template <class T>
@@ -120,25 +81,81 @@ struct HostBuf {
     }
 };
 
+// Pinned copy of a scheduled batch.
+struct PinnedBatch {
+    float *x = nullptr, *y = nullptr, *z = nullptr;
+    int32_t* m = nullptr;
+    ~PinnedBatch()
+    {
+        if (x) cudaFreeHost(x);
+        if (y) cudaFreeHost(y);
+        if (z) cudaFreeHost(z);
+        if (m) cudaFreeHost(m);
+    }
+};
+
+// One event to reconstruct.  Its hits live in the request's own vectors
+// (sbt_server_submit) or in a pinned batch of the open-loop feeder
+// (sbt_server_submit_schedule), kept alive by `hold`.
+struct Request {
+    int64_t id = 0;
+    std::vector<float> ox, oy, oz;
+    std::vector<int32_t> om;
+    const float *x = nullptr, *y = nullptr, *z = nullptr;
+    const int32_t* m = nullptr;
+    int32_t n = 0;
+    bool pinned = false;
+    std::shared_ptr<void> hold;
+    double t_submit = 0.0;
+};
+
+// Pinned downloads of one batch; shared by its requests until all of them
+// are drained or polled, then recycled.
+struct ResultBlock {
+    HostBuf<int32_t> to, ho, th, stat;
+    HostBuf<float> params, chi2;
+    std::vector<int32_t> first_hit;  // batch hit index of each request's first hit
+    int refs = 0;
+};
+
+struct Finished {
+    int64_t id = 0;
+    int32_t status = 0;
+    double latency = 0.0;
+    ResultBlock* block = nullptr;  // null for a failed batch
+    int k = 0;
+};
+
+// A polled request's results, in event-local indices.
+struct Materialized {
+    std::vector<int32_t> hit_offsets, track_hits;
+    std::vector<float> params, chi2;
+};
+
 struct Slot {
     sbt_handle* h = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    bool busy = false;
+    std::atomic<bool> busy{false};
     bool failed = false;
     int64_t bytes = 0;
     std::vector<Request> reqs;
-    int32_t n_events = 0, n_hits = 0;
+    ResultBlock* block = nullptr;
     DevBuf<float> dx, dy, dz, dparams, dchi2;
     DevBuf<int32_t> dm, doff, dto, dho, dth, dndof, dstat, dcounts;
-    HostBuf<float> hx, hy, hz, hparams, hchi2;
-    HostBuf<int32_t> hm, hoff, hto, hho, hth, hstat, hcounts;
+    HostBuf<float> hx, hy, hz;
+    HostBuf<int32_t> hm, hoff;
 };
+
+// Device bytes one batch needs (inputs, outputs and the plain workspace).
+int64_t batch_bytes(int64_t hits, int64_t events)
+{
+    return hits * 96 + events * 320 + (1 << 16);
+}
 
 }  // namespace
 
 struct sbt_server {
-    sbt_handle* parent = nullptr;
     int device = 0;
     int64_t budget = 0;
     int32_t max_batch = 0;
@@ -147,82 +164,47 @@ struct sbt_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request> pending;
     std::deque<Finished> finished;
-    std::map<int64_t, Finished> polled;
+    std::map<int64_t, Materialized> polled;
+    std::vector<ResultBlock*> free_blocks;
+    std::vector<std::unique_ptr<ResultBlock>> all_blocks;
     std::atomic<bool> stop{false};
+    std::atomic<bool> launcher_done{false};
     std::atomic<bool> inject{false};
     int64_t in_flight_bytes = 0;
     double st_completed = 0, st_submitted = 0, st_batches = 0, st_events_batched = 0,
            st_peak_bytes = 0, st_failed = 0;
-    std::string err;
-    std::thread worker;
-    std::thread feeder;
+    std::thread launcher, harvester, feeder;
 };
 
 namespace {
 
-void finish_batch(sbt_server* S, Slot& sl, double t_done)
+void unref_block(sbt_server* S, ResultBlock* b)  // S->mu held
 {
-    std::vector<Finished> out;
-    out.reserve(sl.reqs.size());
-    int32_t off = 0;
-    for (size_t k = 0; k < sl.reqs.size(); k++) {
-        Finished f;
-        f.id = sl.reqs[k].id;
-        f.latency = t_done - sl.reqs[k].t_submit;
-        const int32_t n = sl.reqs[k].n;
-        if (sl.failed) {
-            f.status = SBT_ERR_CUDA;
-            f.hit_offsets.assign(1, 0);
-        } else {
-            f.status = sl.hstat.p[k];
-            const int32_t t0 = sl.hto.p[k], t1 = sl.hto.p[k + 1];
-            f.hit_offsets.resize(t1 - t0 + 1);
-            const int32_t h0 = sl.hho.p[t0];
-            for (int32_t t = t0; t <= t1; t++) f.hit_offsets[t - t0] = sl.hho.p[t] - h0;
-            const int32_t nh = sl.hho.p[t1] - h0;
-            f.track_hits.resize(nh);
-            for (int32_t j = 0; j < nh; j++) f.track_hits[j] = sl.hth.p[h0 + j] - off;
-            f.params.assign(sl.hparams.p + 4 * (size_t)t0, sl.hparams.p + 4 * (size_t)t1);
-            f.chi2.assign(sl.hchi2.p + t0, sl.hchi2.p + t1);
-        }
-        off += n;
-        out.push_back(std::move(f));
-    }
-    std::lock_guard<std::mutex> lk(S->mu);
-    for (auto& f : out) S->finished.push_back(std::move(f));
-    S->st_completed += (double)out.size();
-    if (sl.failed) S->st_failed += 1;
-    S->in_flight_bytes -= sl.bytes;
-    sl.busy = false;
-    sl.failed = false;
-    sl.reqs.clear();
-    S->cv_done.notify_all();
+    if (b && --b->refs == 0) S->free_blocks.push_back(b);
 }
 
-// Launch one admitted group on a slot.  Returns false on a CUDA error (the
-// group is then completed with an error status).
-bool launch_batch(sbt_server* S, Slot& sl)
+// Enqueue one admitted group on a slot.  Returns false on a CUDA error.
+bool launch_batch(Slot& sl)
 {
     const int32_t E = (int32_t)sl.reqs.size();
     int64_t H64 = 0;
     for (auto& r : sl.reqs) H64 += (int64_t)r.n;
     const int32_t H = (int32_t)H64;
     const size_t capT = (size_t)H / 3 + 1, capH = (size_t)H + 1;
+    ResultBlock& B = *sl.block;
     cudaError_t e = cudaSuccess;
     auto need = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
     };
-    // a group of scheduled events that are consecutive in one pinned batch is
-    // uploaded directly; anything else is packed into the slot's staging
     bool direct = sl.reqs[0].pinned;
     for (int32_t k = 1; k < E && direct; k++) {
         const Request& p = sl.reqs[k - 1];
         const Request& r = sl.reqs[k];
         direct = r.pinned && r.x == p.x + p.n && r.y == p.y + p.n && r.z == p.z + p.n && r.m == p.m + p.n;
     }
-    need(sl.hoff.reserve(E + 1)); need(sl.hto.reserve(E + 1)); need(sl.hho.reserve(capT + 1));
-    need(sl.hth.reserve(capH)); need(sl.hparams.reserve(4 * capT)); need(sl.hchi2.reserve(capT));
-    need(sl.hstat.reserve(E)); need(sl.hcounts.reserve(4));
+    need(sl.hoff.reserve(E + 1));
+    need(B.to.reserve(E + 1)); need(B.ho.reserve(capT + 1)); need(B.th.reserve(capH));
+    need(B.params.reserve(4 * capT)); need(B.chi2.reserve(capT)); need(B.stat.reserve(E));
     if (!direct) {
         need(sl.hx.reserve(H)); need(sl.hy.reserve(H)); need(sl.hz.reserve(H)); need(sl.hm.reserve(H));
     }
@@ -231,11 +213,13 @@ bool launch_batch(sbt_server* S, Slot& sl)
     need(sl.dth.reserve(capH)); need(sl.dparams.reserve(4 * capT)); need(sl.dchi2.reserve(capT));
     need(sl.dndof.reserve(capT)); need(sl.dstat.reserve(E)); need(sl.dcounts.reserve(4));
     if (e != cudaSuccess) return false;
+    B.first_hit.resize(E);
     int32_t o = 0;
     for (int32_t k = 0; k < E; k++) {
         const Request& r = sl.reqs[k];
         const size_t n = (size_t)r.n;
         sl.hoff.p[k] = o;
+        B.first_hit[k] = o;
         if (!direct && n) {
             std::memcpy(sl.hx.p + o, r.x, 4 * n);
             std::memcpy(sl.hy.p + o, r.y, 4 * n);
@@ -246,15 +230,11 @@ bool launch_batch(sbt_server* S, Slot& sl)
     }
     sl.hoff.p[E] = o;
     cudaStream_t s = sl.stream;
-    const float* sx = direct ? sl.reqs[0].x : sl.hx.p;
-    const float* sy = direct ? sl.reqs[0].y : sl.hy.p;
-    const float* sz = direct ? sl.reqs[0].z : sl.hz.p;
-    const int32_t* sm = direct ? sl.reqs[0].m : sl.hm.p;
     if (H) {
-        need(cudaMemcpyAsync(sl.dx.p, sx, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
-        need(cudaMemcpyAsync(sl.dy.p, sy, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
-        need(cudaMemcpyAsync(sl.dz.p, sz, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
-        need(cudaMemcpyAsync(sl.dm.p, sm, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dx.p, direct ? sl.reqs[0].x : sl.hx.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dy.p, direct ? sl.reqs[0].y : sl.hy.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dz.p, direct ? sl.reqs[0].z : sl.hz.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        need(cudaMemcpyAsync(sl.dm.p, direct ? sl.reqs[0].m : sl.hm.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
     }
     need(cudaMemcpyAsync(sl.doff.p, sl.hoff.p, 4 * (size_t)(E + 1), cudaMemcpyHostToDevice, s));
     if (e != cudaSuccess) return false;
@@ -271,77 +251,131 @@ bool launch_batch(sbt_server* S, Slot& sl)
     out.cap_hits = (int32_t)capH;
     if (sbt_reconstruct(sl.h, sl.dx.p, sl.dy.p, sl.dz.p, sl.dm.p, sl.doff.p, E, H, &out, s) != SBT_OK)
         return false;
-    need(cudaMemcpyAsync(sl.hto.p, sl.dto.p, 4 * (size_t)(E + 1), cudaMemcpyDeviceToHost, s));
-    need(cudaMemcpyAsync(sl.hstat.p, sl.dstat.p, 4 * (size_t)E, cudaMemcpyDeviceToHost, s));
-    need(cudaMemcpyAsync(sl.hho.p, sl.dho.p, 4 * (capT + 1), cudaMemcpyDeviceToHost, s));
-    need(cudaMemcpyAsync(sl.hth.p, sl.dth.p, 4 * capH, cudaMemcpyDeviceToHost, s));
-    need(cudaMemcpyAsync(sl.hparams.p, sl.dparams.p, 16 * capT, cudaMemcpyDeviceToHost, s));
-    need(cudaMemcpyAsync(sl.hchi2.p, sl.dchi2.p, 4 * capT, cudaMemcpyDeviceToHost, s));
+    need(cudaMemcpyAsync(B.to.p, sl.dto.p, 4 * (size_t)(E + 1), cudaMemcpyDeviceToHost, s));
+    need(cudaMemcpyAsync(B.stat.p, sl.dstat.p, 4 * (size_t)E, cudaMemcpyDeviceToHost, s));
+    need(cudaMemcpyAsync(B.ho.p, sl.dho.p, 4 * (capT + 1), cudaMemcpyDeviceToHost, s));
+    need(cudaMemcpyAsync(B.th.p, sl.dth.p, 4 * capH, cudaMemcpyDeviceToHost, s));
+    need(cudaMemcpyAsync(B.params.p, sl.dparams.p, 16 * capT, cudaMemcpyDeviceToHost, s));
+    need(cudaMemcpyAsync(B.chi2.p, sl.dchi2.p, 4 * capT, cudaMemcpyDeviceToHost, s));
     need(cudaEventRecord(sl.done, s));
     return e == cudaSuccess;
 }
 
-void worker_loop(sbt_server* S)
+void launcher_loop(sbt_server* S)
 {
     cudaSetDevice(S->device);
-    while (true) {
-        bool did = false;
-        // harvest
-        for (auto& up : S->slots) {
-            Slot& sl = *up;
-            if (!sl.busy) continue;
-            if (sl.failed || cudaEventQuery(sl.done) == cudaSuccess) {
-                finish_batch(S, sl, now_s());
-                did = true;
+    for (;;) {
+        Slot* free_slot = nullptr;
+        for (auto& up : S->slots)
+            if (!up->busy.load(std::memory_order_acquire)) {
+                free_slot = up.get();
+                break;
             }
-        }
-        // admit
-        for (auto& up : S->slots) {
-            Slot& sl = *up;
-            if (sl.busy) continue;
-            std::vector<Request> take;
-            int64_t bytes = 0, hits = 0;
-            {
-                std::lock_guard<std::mutex> lk(S->mu);
+        std::vector<Request> take;
+        int64_t bytes = 0;
+        ResultBlock* block = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (free_slot) {
+                int64_t hits = 0;
                 while (!S->pending.empty() && (int32_t)take.size() < S->max_batch) {
                     const Request& r = S->pending.front();
-                    int64_t b = batch_bytes(hits + (int64_t)r.n, (int64_t)take.size() + 1);
-                    if (S->in_flight_bytes + b > S->budget && !take.empty()) break;
-                    if (S->in_flight_bytes + b > S->budget && S->in_flight_bytes > 0) break;
+                    const int64_t b = batch_bytes(hits + (int64_t)r.n, (int64_t)take.size() + 1);
+                    if (S->in_flight_bytes + b > S->budget && (!take.empty() || S->in_flight_bytes > 0))
+                        break;
                     hits += (int64_t)r.n;
                     bytes = b;
                     take.push_back(std::move(S->pending.front()));
                     S->pending.pop_front();
                 }
-                if (take.empty()) break;
-                S->in_flight_bytes += bytes;
-                S->st_peak_bytes = std::max(S->st_peak_bytes, (double)S->in_flight_bytes);
-                S->st_batches += 1;
-                S->st_events_batched += (double)take.size();
             }
-            sl.reqs = std::move(take);
-            sl.bytes = bytes;
-            sl.busy = true;
-            if (S->inject.exchange(false)) {
-                sl.failed = true;  // host-side failure: nothing was enqueued
-            } else if (!launch_batch(S, sl)) {
-                // drain whatever part of the batch was enqueued before the
-                // slot's buffers are reused
-                cudaStreamSynchronize(sl.stream);
-                sl.failed = true;
+            if (take.empty()) {
+                if (S->stop.load() && S->pending.empty()) break;
+                S->cv_work.wait_for(lk, std::chrono::microseconds(50));
+                continue;
             }
-            did = true;
+            S->in_flight_bytes += bytes;
+            S->st_peak_bytes = std::max(S->st_peak_bytes, (double)S->in_flight_bytes);
+            S->st_batches += 1;
+            S->st_events_batched += (double)take.size();
+            if (S->free_blocks.empty()) {
+                S->all_blocks.push_back(std::make_unique<ResultBlock>());
+                block = S->all_blocks.back().get();
+            } else {
+                block = S->free_blocks.back();
+                S->free_blocks.pop_back();
+            }
         }
-        if (S->stop.load()) {
-            bool idle = true;
-            for (auto& up : S->slots) idle = idle && !up->busy;
-            std::lock_guard<std::mutex> lk(S->mu);
-            if (idle && S->pending.empty()) break;
+        Slot& sl = *free_slot;
+        sl.reqs = std::move(take);
+        sl.bytes = bytes;
+        sl.block = block;
+        sl.failed = false;
+        if (S->inject.exchange(false)) {
+            sl.failed = true;  // host-side failure: nothing was enqueued
+        } else if (!launch_batch(sl)) {
+            cudaStreamSynchronize(sl.stream);  // drain what was enqueued before reuse
+            sl.failed = true;
         }
-        if (!did) {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        sl.busy.store(true, std::memory_order_release);
+    }
+    S->launcher_done.store(true);
+}
+
+void harvest(sbt_server* S, Slot& sl)
+{
+    const double t_done = now_s();
+    std::vector<Finished> out(sl.reqs.size());
+    ResultBlock* B = sl.block;
+    for (size_t k = 0; k < sl.reqs.size(); k++) {
+        Finished& f = out[k];
+        f.id = sl.reqs[k].id;
+        f.latency = t_done - sl.reqs[k].t_submit;
+        f.k = (int)k;
+        if (sl.failed) {
+            f.status = SBT_ERR_CUDA;
+            f.block = nullptr;
+        } else {
+            f.status = B->stat.p[k];
+            f.block = B;
         }
+    }
+    sl.reqs.clear();  // releases the pinned batches the uploads read from
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (sl.failed) {
+            S->free_blocks.push_back(B);
+            S->st_failed += 1;
+        } else {
+            B->refs = (int)out.size();
+            if (out.empty()) S->free_blocks.push_back(B);
+        }
+        for (auto& f : out) S->finished.push_back(f);
+        S->st_completed += (double)out.size();
+        S->in_flight_bytes -= sl.bytes;
+    }
+    sl.block = nullptr;
+    sl.busy.store(false, std::memory_order_release);
+    S->cv_done.notify_all();
+    S->cv_work.notify_one();
+}
+
+void harvester_loop(sbt_server* S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        bool did = false, any_busy = false;
+        for (auto& up : S->slots) {
+            Slot& sl = *up;
+            if (!sl.busy.load(std::memory_order_acquire)) continue;
+            any_busy = true;
+            if (sl.failed || cudaEventQuery(sl.done) == cudaSuccess) {
+                harvest(S, sl);
+                did = true;
+            }
+        }
+        if (!any_busy && S->launcher_done.load()) break;
+        if (!did) std::this_thread::sleep_for(std::chrono::microseconds(10));
     }
 }
 
@@ -357,7 +391,6 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
         return SBT_ERR_ARG;
     *out = nullptr;
     auto* S = new sbt_server();
-    S->parent = h;
     S->budget = memory_budget_bytes;
     S->max_batch = max_batch_events;
     cudaError_t e = cudaGetDevice(&S->device);
@@ -377,6 +410,7 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
     cfg.hit_sigma = C.sigma;
     cfg.max_hits_per_event = C.nmax;
     cfg.max_forming_tracks = C.fcap;
+    cfg.threads_per_block = sbt::handle_plain_threads(h);
     for (int i = 0; i < max_streams && e == cudaSuccess; i++) {
         auto sl = std::make_unique<Slot>();
         if (sbt_create(&g, &cfg, &sl->h) != SBT_OK) {
@@ -396,7 +430,8 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
         delete S;
         return SBT_ERR_CUDA;
     }
-    S->worker = std::thread(worker_loop, S);
+    S->launcher = std::thread(launcher_loop, S);
+    S->harvester = std::thread(harvester_loop, S);
     *out = S;
     return SBT_OK;
 }
@@ -427,16 +462,12 @@ sbt_status sbt_server_submit(sbt_server* S, int64_t request_id, const float* x, 
     return SBT_OK;
 }
 
-/*
- * Open-loop load: a native thread submits event e of the host batch (x, y, z,
- * module [event_offsets[e] .. event_offsets[e+1])) at arrival_s[e] seconds
- * after this call, with request id first_id + e.  Returns at once.
- */
 sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float* y, const float* z,
                                       const int32_t* module, const int32_t* event_offsets,
                                       int32_t n_events, const double* arrival_s, int64_t first_id)
 {
     if (!S || n_events < 0 || !event_offsets || !arrival_s) return SBT_ERR_ARG;
+    if (S->stop.load()) return SBT_ERR_STATE;
     if (S->feeder.joinable()) S->feeder.join();
     const int32_t H = event_offsets[n_events];
     auto batch = std::make_shared<PinnedBatch>();
@@ -454,22 +485,21 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
     std::vector<double> at(arrival_s, arrival_s + n_events);
     S->feeder = std::thread([S, batch, vo = std::move(vo), at = std::move(at), first_id, n_events]() {
         const auto t0 = Clock::now();
+        auto due_at = [&](int32_t e) {
+            return t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(at[e]));
+        };
         int32_t e = 0;
         while (e < n_events && !S->stop.load()) {
-            const auto due = t0 + std::chrono::duration_cast<Clock::duration>(
-                                      std::chrono::duration<double>(at[e]));
             auto now = Clock::now();
-            if (now < due) {
-                auto left = due - now;
+            if (now < due_at(e)) {
+                auto left = due_at(e) - now;
                 if (left > std::chrono::microseconds(200))
                     std::this_thread::sleep_for(left - std::chrono::microseconds(100));
                 continue;
             }
-            // submit every event that is due
-            std::vector<Request> due_reqs;
+            std::vector<Request> due;
             const double ts = now_s();
-            while (e < n_events && t0 + std::chrono::duration_cast<Clock::duration>(
-                                          std::chrono::duration<double>(at[e])) <= now) {
+            while (e < n_events && due_at(e) <= now) {
                 Request r;
                 r.id = first_id + e;
                 const int32_t lo = vo[e];
@@ -481,13 +511,13 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
                 r.pinned = true;
                 r.hold = batch;
                 r.t_submit = ts;
-                due_reqs.push_back(std::move(r));
+                due.push_back(std::move(r));
                 e++;
             }
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                for (auto& r : due_reqs) S->pending.push_back(std::move(r));
-                S->st_submitted += (double)due_reqs.size();
+                for (auto& r : due) S->pending.push_back(std::move(r));
+                S->st_submitted += (double)due.size();
             }
             S->cv_work.notify_one();
         }
@@ -495,11 +525,6 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
     return SBT_OK;
 }
 
-/*
- * Finished requests for consumers that only need their completion: up to
- * max_results (request id, status, latency) triples; the results are released
- * at once.  Waits at most timeout_s for the first one.
- */
 sbt_status sbt_server_drain(sbt_server* S, int64_t* ids, int32_t* status, double* latency_s,
                             int32_t max_results, int32_t* n_out, double timeout_s)
 {
@@ -517,6 +542,7 @@ sbt_status sbt_server_drain(sbt_server* S, int64_t* ids, int32_t* status, double
         ids[k] = f.id;
         status[k] = f.status;
         latency_s[k] = f.latency;
+        unref_block(S, f.block);
         S->finished.pop_front();
         k++;
     }
@@ -529,28 +555,56 @@ sbt_status sbt_server_poll(sbt_server* S, sbt_result* results, int32_t max_resul
 {
     if (!S || !n_out || max_results < 0 || (max_results > 0 && !results)) return SBT_ERR_ARG;
     *n_out = 0;
-    std::unique_lock<std::mutex> lk(S->mu);
-    if (S->finished.empty() && timeout_s > 0)
-        S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
-                            [&] { return !S->finished.empty(); });
-    if (S->finished.empty()) return timeout_s > 0 ? SBT_ERR_TIMEOUT : SBT_OK;
-    int32_t k = 0;
-    while (k < max_results && !S->finished.empty()) {
-        Finished f = std::move(S->finished.front());
-        S->finished.pop_front();
-        auto it = S->polled.emplace(f.id, std::move(f)).first;
-        Finished& g = it->second;
-        sbt_result& r = results[k++];
-        r.request_id = g.id;
-        r.status = g.status;
+    std::vector<Finished> got;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->finished.empty() && timeout_s > 0)
+            S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                [&] { return !S->finished.empty(); });
+        if (S->finished.empty()) return timeout_s > 0 ? SBT_ERR_TIMEOUT : SBT_OK;
+        while ((int32_t)got.size() < max_results && !S->finished.empty()) {
+            got.push_back(S->finished.front());
+            S->finished.pop_front();
+        }
+    }
+    // event-local copies of each request's tracks, made outside the lock (the
+    // result block stays referenced until then)
+    std::vector<Materialized> mats(got.size());
+    for (size_t i = 0; i < got.size(); i++) {
+        const Finished& f = got[i];
+        Materialized& m = mats[i];
+        if (!f.block) {
+            m.hit_offsets.assign(1, 0);
+            continue;
+        }
+        const ResultBlock& B = *f.block;
+        const int32_t t0 = B.to.p[f.k], t1 = B.to.p[f.k + 1];
+        const int32_t h0 = B.ho.p[t0];
+        m.hit_offsets.resize(t1 - t0 + 1);
+        for (int32_t t = t0; t <= t1; t++) m.hit_offsets[t - t0] = B.ho.p[t] - h0;
+        const int32_t nh = B.ho.p[t1] - h0;
+        const int32_t base = B.first_hit[f.k];
+        m.track_hits.resize(nh);
+        for (int32_t j = 0; j < nh; j++) m.track_hits[j] = B.th.p[h0 + j] - base;
+        m.params.assign(B.params.p + 4 * (size_t)t0, B.params.p + 4 * (size_t)t1);
+        m.chi2.assign(B.chi2.p + t0, B.chi2.p + t1);
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t i = 0; i < got.size(); i++) {
+        const Finished& f = got[i];
+        unref_block(S, f.block);
+        Materialized& g = S->polled[f.id] = std::move(mats[i]);
+        sbt_result& r = results[i];
+        r.request_id = f.id;
+        r.status = f.status;
         r.n_tracks = (int32_t)g.hit_offsets.size() - 1;
         r.hit_offsets = g.hit_offsets.data();
         r.track_hits = g.track_hits.data();
         r.params = g.params.data();
         r.chi2 = g.chi2.data();
-        r.latency_s = g.latency;
+        r.latency_s = f.latency;
     }
-    *n_out = k;
+    *n_out = (int32_t)got.size();
     return SBT_OK;
 }
 
@@ -589,7 +643,8 @@ sbt_status sbt_server_destroy(sbt_server* S)
     if (S->feeder.joinable()) S->feeder.join();
     S->stop.store(true);
     S->cv_work.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    if (S->launcher.joinable()) S->launcher.join();
+    if (S->harvester.joinable()) S->harvester.join();
     for (auto& up : S->slots) {
         Slot& sl = *up;
         cudaStreamSynchronize(sl.stream);
@@ -597,11 +652,13 @@ sbt_status sbt_server_destroy(sbt_server* S)
         sl.dto.release(); sl.dho.release(); sl.dth.release(); sl.dparams.release();
         sl.dchi2.release(); sl.dndof.release(); sl.dstat.release(); sl.dcounts.release();
         sl.hx.release(); sl.hy.release(); sl.hz.release(); sl.hm.release(); sl.hoff.release();
-        sl.hto.release(); sl.hho.release(); sl.hth.release(); sl.hparams.release();
-        sl.hchi2.release(); sl.hstat.release(); sl.hcounts.release();
         cudaEventDestroy(sl.done);
         cudaStreamDestroy(sl.stream);
         sbt_destroy(sl.h);
+    }
+    for (auto& b : S->all_blocks) {
+        b->to.release(); b->ho.release(); b->th.release(); b->stat.release();
+        b->params.release(); b->chi2.release();
     }
     delete S;
     return SBT_OK;
