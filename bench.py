@@ -119,7 +119,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def serve(sbt, h, ev, rate_hz, budget_bytes, streams=4, max_batch=512, timeout=120.0):
+def serve(sbt, h, ev, rate_hz, budget_bytes, streams=8, max_batch=512, timeout=120.0):
     """Open-loop Poisson arrivals at rate_hz into the request loop; returns
     events/s (completions over the span from first arrival to last
     completion) and submit-to-done latency percentiles."""

@@ -26,9 +26,12 @@ constexpr int kMaxChunks = 16;
 struct Arena {
     void* base = nullptr;
     size_t bytes = 0;
+    // Grows geometrically: freeing device memory synchronises the device, so
+    // workspaces must not be reallocated for every slightly larger batch.
     cudaError_t reserve(size_t need)
     {
         if (need <= bytes) return cudaSuccess;
+        if (bytes) need = std::max(need, bytes + bytes / 2);
         if (base) {
             cudaError_t e = cudaFree(base);
             base = nullptr;

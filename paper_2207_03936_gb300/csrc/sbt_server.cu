@@ -44,6 +44,7 @@ struct DevBuf {
     cudaError_t reserve(size_t want)
     {
         if (want <= n) return cudaSuccess;
+        if (n) want = std::max(want, n + n / 2);  // grow geometrically: frees synchronise
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
@@ -66,6 +67,7 @@ struct HostBuf {
     cudaError_t reserve(size_t want)
     {
         if (want <= n) return cudaSuccess;
+        if (n) want = std::max(want, n + n / 2);
         if (p) cudaFreeHost(p);
         p = nullptr;
         n = 0;
