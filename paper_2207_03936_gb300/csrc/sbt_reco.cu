@@ -273,7 +273,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 // ------------------------------------------------------------- sorting ---
 
 constexpr int kSortThreads = 1024;
-constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortWarps = 8;  // warps that build digit histograms and scatter (the rest wait)
 
 // Shared memory of the sort kernel: keys and indices ping-pong (12 B per hit)
 // and the per-warp digit histograms.
@@ -312,7 +312,7 @@ __device__ void radix_pass(const uint32_t* ks, const uint16_t* is, uint32_t* kd,
     __syncthreads();
     const int chunk = (n + NW - 1) / NW;
     const int beg = warp * chunk;
-    const int end = min(n, beg + chunk);
+    const int end = warp < NW ? min(n, beg + chunk) : 0;
     for (int b = beg; b < end; b += 32) {
         int j = b + lane;
         bool v = j < end;
@@ -477,45 +477,61 @@ __device__ __forceinline__ uint32_t phi16_window(float x, float y)
     return (uint32_t)__float2int_rn(p * 10430.378f) & 0xFFFFu;
 }
 
-// Best unflagged hit on module [b0, b0 + nb) for the prediction (xp, yp)
-// with scatter < cut.  Hits outside a phi window around the prediction cannot
-// pass the cut: a hit within d = sqrt(cut) of the prediction differs from it
-// in angle by at most asin(d / r) <= d / sqrt(r^2 - d^2); the half-width adds
-// 1/16 of that plus 16 phi16 units for the rounding and arctangent error of
-// both phi values and for the approximate arithmetic of the bound itself.
-// Predictions near the axis (r <= 2 d) scan the whole module.  The scatter
-// of every hit in the window is computed exactly (rounded operations), and
-// `better(sc, b)` orders candidates.
+// Phi window of a prediction (xp, yp) for a scatter cut: hits outside it
+// cannot pass the cut.  A hit within d = sqrt(cut) of the prediction differs
+// from it in angle by at most asin(d / r) <= d / sqrt(r^2 - d^2); the
+// half-width adds 1/16 of that plus 16 phi16 units for the rounding and
+// arctangent error of both phi values and for the approximate arithmetic of
+// the bound itself.  Predictions near the axis (r <= 2 d) get no window (the
+// whole module is scanned).
+__device__ __forceinline__ bool window_of(float xp, float yp, float cut, float sqrt_cut, uint32_t& lo,
+                                          uint32_t& width)
+{
+    const float rp2 = xp * xp + yp * yp;
+    if (rp2 < 1.0e30f && rp2 > 4.0f * cut) {
+        const float wf = sqrt_cut * rsqrtf(rp2 - cut) * (10430.378f * 1.0625f);
+        if (wf < 16000.0f) {
+            const uint32_t W = (uint32_t)wf + 16u;
+            lo = (phi16_window(xp, yp) - W) & 0xFFFFu;
+            width = 2u * W;
+            return true;
+        }
+    }
+    lo = 0;
+    width = 0xFFFFu;
+    return false;
+}
+
+// Visits the unflagged hits of module [b0, b0 + nb) inside the window that
+// starts at sorted index lo_idx (all hits when not windowed); the scatter of
+// every visited hit is computed exactly (rounded operations) and
+// `better(sc, b)` orders candidates under the cut.
+template <class Better, class Take>
+__device__ __forceinline__ void scan_from(const Smem& S, const Region& R, int b0, int nb, float xp,
+                                          float yp, float cut, bool windowed, int lo_idx,
+                                          uint32_t lo, uint32_t width, Better better, Take take)
+{
+    for (int k = 0; k < nb; k++) {
+        int e = lo_idx + k;
+        if (e >= nb) e -= nb;
+        const int b = b0 + e;
+        if (windowed && (((uint32_t)R.phi[b] - lo) & 0xFFFFu) > width) break;
+        if (flagged(S, b)) continue;
+        const float sc = scatter_of(R.coords[b], xp, yp);
+        if (sc < cut && better(sc, b)) take(sc, b);
+    }
+}
+
 template <class Better, class Take>
 __device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int b0, int nb, float xp,
                                             float yp, float cut, float sqrt_cut, Better better,
                                             Take take)
 {
     if (nb <= 0) return;
-    float rp2 = xp * xp + yp * yp;
-    int lo_idx = 0;
-    uint32_t lo = 0, width = 0xFFFFu;
-    bool windowed = false;
-    if (rp2 < 1.0e30f && rp2 > 4.0f * cut) {
-        float wf = sqrt_cut * rsqrtf(rp2 - cut) * (10430.378f * 1.0625f);
-        if (wf < 16000.0f) {
-            uint32_t W = (uint32_t)wf + 16u;
-            uint32_t php = phi16_window(xp, yp);
-            lo = (php - W) & 0xFFFFu;
-            width = 2u * W;
-            lo_idx = lower_bound16(R.phi + b0, nb, lo);
-            windowed = true;
-        }
-    }
-    for (int k = 0; k < nb; k++) {
-        int e = lo_idx + k;
-        if (e >= nb) e -= nb;
-        int b = b0 + e;
-        if (windowed && (((uint32_t)R.phi[b] - lo) & 0xFFFFu) > width) break;
-        if (flagged(S, b)) continue;
-        float sc = scatter_of(R.coords[b], xp, yp);
-        if (sc < cut && better(sc, b)) take(sc, b);
-    }
+    uint32_t lo, width;
+    const bool windowed = window_of(xp, yp, cut, sqrt_cut, lo, width);
+    const int lo_idx = windowed ? lower_bound16(R.phi + b0, nb, lo) : 0;
+    scan_from(S, R, b0, nb, xp, yp, cut, windowed, lo_idx, lo, width, better, take);
 }
 
 // First index in keys[0, n) whose upper 16 bits are >= v.
@@ -530,6 +546,67 @@ __device__ __forceinline__ int lower_bound_hi16(const uint32_t* keys, int n, uin
             hi = mid;
     }
     return lo;
+}
+
+constexpr int kSeedBatch = 4;
+
+// Candidates a[0, na) of one middle hit, processed together: extrapolations,
+// then the binary searches of their windows in lockstep (independent loads in
+// flight), then the window scans.  Keeps the best (scatter, a, b).
+__device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& S, const Region& R,
+                                                int i0, int ni, float4 Cc, float zi, float sqrt_cut,
+                                                const int* a, int na, bool& have, float& best_sc,
+                                                int& best_a, int& best_b)
+{
+    float xp[kSeedBatch], yp[kSeedBatch];
+    uint32_t lo[kSeedBatch], width[kSeedBatch];
+    int L[kSeedBatch], H[kSeedBatch];
+    bool win[kSeedBatch];
+#pragma unroll
+    for (int u = 0; u < kSeedBatch; u++) {
+        L[u] = 0;
+        H[u] = 0;
+        win[u] = false;
+        if (u < na) {
+            extrapolate(R.coords[a[u]], Cc, zi, xp[u], yp[u]);
+            win[u] = window_of(xp[u], yp[u], C.S_seed, sqrt_cut, lo[u], width[u]);
+            H[u] = win[u] ? ni : 0;
+        }
+    }
+    const uint16_t* phi = R.phi + i0;
+    for (int it = 0; it < 17; it++) {
+        bool active = false;
+#pragma unroll
+        for (int u = 0; u < kSeedBatch; u++) active |= L[u] < H[u];
+        if (!active) break;
+#pragma unroll
+        for (int u = 0; u < kSeedBatch; u++) {
+            if (L[u] < H[u]) {
+                const int mid = (L[u] + H[u]) >> 1;
+                if ((uint32_t)phi[mid] < lo[u])
+                    L[u] = mid + 1;
+                else
+                    H[u] = mid;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kSeedBatch; u++) {
+        if (u >= na) continue;
+        const int au = a[u];
+        scan_from(
+            S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u],
+            [&](float sc, int b) {
+                return !have || sc < best_sc ||
+                       (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
+            },
+            [&](float sc, int b) {
+                have = true;
+                best_sc = sc;
+                best_a = au;
+                best_b = b;
+            });
+    }
 }
 
 // Seeding for middle hit c on module s+1: the unflagged hits of module s
@@ -553,6 +630,8 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int
     bool have = false;
     float best_sc = 0.0f;
     int best_a = 0, best_b = 0;
+    int cand[kSeedBatch];
+    int nc = 0;
     for (int visited = 0; visited < nu; visited++) {
         const int iu = up >= nu ? up - nu : up;
         const int id = dn < 0 ? dn + nu : dn;
@@ -572,21 +651,14 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int
         if (found >= C.K && d > dK) break;
         found++;
         if (found == C.K) dK = d;
-        float xp, yp;
-        extrapolate(R.coords[a], Cc, zi, xp, yp);
-        scan_window(
-            S, R, i0, ni, xp, yp, C.S_seed, sqrt_cut,
-            [&](float sc, int b) {
-                return !have || sc < best_sc ||
-                       (sc == best_sc && (a < best_a || (a == best_a && b < best_b)));
-            },
-            [&](float sc, int b) {
-                have = true;
-                best_sc = sc;
-                best_a = a;
-                best_b = b;
-            });
+        cand[nc++] = a;
+        if (nc == kSeedBatch) {
+            seed_candidates(C, S, R, i0, ni, Cc, zi, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
+            nc = 0;
+        }
     }
+    if (nc > 0)
+        seed_candidates(C, S, R, i0, ni, Cc, zi, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
     if (have) {
         oa = best_a;
         ob = best_b;
