@@ -273,7 +273,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 // ------------------------------------------------------------- sorting ---
 
 constexpr int kSortThreads = 1024;
-constexpr int kSortWarps = 8;  // warps that build digit histograms and scatter (the rest wait)
+constexpr int kSortWarps = 16;  // warps that build digit histograms and scatter (the rest wait)
 
 // Shared memory of the sort kernel: keys and indices ping-pong (12 B per hit)
 // and the per-warp digit histograms.
@@ -548,7 +548,7 @@ __device__ __forceinline__ int lower_bound_hi16(const uint32_t* keys, int n, uin
     return lo;
 }
 
-constexpr int kSeedBatch = 4;
+constexpr int kSeedBatch = 1;
 
 // Candidates a[0, na) of one middle hit, processed together: extrapolations,
 // then the binary searches of their windows in lockstep (independent loads in
@@ -861,10 +861,15 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S,
                 bool won = false;
                 if (T.cand != kNone) {
                     const unsigned long long k = claim_key(tag, T.sc, T.key);
-                    won = __ldcg(&R.claim[T.cand]) == k;
-                    if (won && T.nh == 3)
-                        won = __ldcg(&R.claim[T.h0]) == k && __ldcg(&R.claim[T.h1]) == k &&
-                              __ldcg(&R.claim[T.h2]) == k;
+                    // all claim words loaded at once (one round trip)
+                    const unsigned long long c0 = __ldcg(&R.claim[T.cand]);
+                    unsigned long long c1 = k, c2 = k, c3 = k;
+                    if (T.nh == 3) {
+                        c1 = __ldcg(&R.claim[T.h0]);
+                        c2 = __ldcg(&R.claim[T.h1]);
+                        c3 = __ldcg(&R.claim[T.h2]);
+                    }
+                    won = c0 == k && c1 == k && c2 == k && c3 == k;
                 }
                 if (won) {
                     set_flag(S, T.cand);
@@ -954,7 +959,10 @@ __device__ void tracklet_filter(const DevConfig& C, const Region& R, const Smem&
 }
 
 // Canonical order (smallest input hit index), staging of the hit lists and
-// the least-squares fit of every track on the cached sorted coordinates.
+// the least-squares fit of every track on the sorted coordinates.  Each
+// track's linked hit list is walked once, into `pos` at the track's place in
+// found order; ranks then come from a running count of marks over input
+// indices, and the hit writes and fit passes read `pos` (independent loads).
 template <int NT>
 __device__ void output_stage(const DevConfig& C, int e, int off, int n, const Region& R,
                              const Smem& S, const Staging& G, const sbt_tracks& out)
@@ -963,19 +971,38 @@ __device__ void output_stage(const DevConfig& C, int e, int off, int n, const Re
     const int T = S.misc[kNFin];
     uint16_t* mark = R.mark;
     uint16_t* pos = R.pos;
+    // found-order starts (fin_start holds them until the canonical starts replace them)
+    {
+        const int chunk = (T + NT - 1) / NT;
+        const int beg = min(T, tid * chunk), end = min(T, beg + chunk);
+        int cnt = 0;
+        for (int k = beg; k < end; k++) cnt += (int)(R.finals[k] >> 16);
+        int total;
+        int st = block_exclusive_scan<NT>(cnt, S.wsum, &total);
+        for (int k = beg; k < end; k++) {
+            R.fin_rank[k] = st;  // found-order start, replaced by the rank below
+            st += (int)(R.finals[k] >> 16);
+        }
+    }
+    __syncthreads();
     for (int k = tid; k < T; k += NT) {
-        uint32_t v = R.finals[k];
-        int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
+        const uint32_t v = R.finals[k];
+        int q = (int)(v & 0xFFFF);
+        const int nh = (int)(v >> 16);
+        const int u = R.fin_rank[k];
         int mn = INT_MAX;
-        for (int j = 0; j < nh; j++) {
-            int i = __float_as_int(R.coords[q].w);
+        for (int j = nh - 1; j >= 0; j--) {
+            pos[u + j] = (uint16_t)q;
+            const int nq = R.prev[q];
+            const int i = __float_as_int(R.coords[q].w);
             mn = i < mn ? i : mn;
-            q = R.prev[q];
+            q = nq;
         }
         mark[mn] = (uint16_t)k;
     }
     __syncthreads();
-    // ranks: running count of marks over input indices
+    // ranks: running count of marks over input indices; a track's found-order
+    // start moves to fin_start[rank]
     {
         const int chunk = (n + NT - 1) / NT;
         const int beg = min(n, tid * chunk), end = min(n, beg + chunk);
@@ -984,13 +1011,19 @@ __device__ void output_stage(const DevConfig& C, int e, int off, int n, const Re
         int total;
         int r = block_exclusive_scan<NT>(cnt, S.wsum, &total);
         for (int i = beg; i < end; i++)
-            if (mark[i] != kNone) R.fin_rank[mark[i]] = r++;
+            if (mark[i] != kNone) {
+                const int k = mark[i];
+                R.fin_start[r] = R.fin_rank[k];
+                R.fin_rank[k] = r++;
+            }
     }
     __syncthreads();
     const int64_t slot0 = (int64_t)off / 3 + e;
     uint8_t* len = G.len + slot0;
     for (int k = tid; k < T; k += NT) len[R.fin_rank[k]] = (uint8_t)(R.finals[k] >> 16);
     __syncthreads();
+    // canonical starts (scan of lengths in rank order); each thread then
+    // handles whole tracks in rank order
     int H;
     {
         const int chunk = (T + NT - 1) / NT;
@@ -999,31 +1032,21 @@ __device__ void output_stage(const DevConfig& C, int e, int off, int n, const Re
         for (int r = beg; r < end; r++) cnt += len[r];
         int st = block_exclusive_scan<NT>(cnt, S.wsum, &H);
         for (int r = beg; r < end; r++) {
-            R.fin_start[r] = st;
-            st += len[r];
+            const int nh = len[r];
+            const int u = R.fin_start[r];
+            for (int j = 0; j < nh; j++) G.hits[(int64_t)off + st + j] = off + __float_as_int(R.coords[pos[u + j]].w);
+            float p[4], chi2;
+            fit_line(
+                nh,
+                [&](int i) {
+                    const float4 c = R.coords[pos[u + i]];
+                    return make_float3(c.x, c.y, c.z);
+                },
+                C.sigma, p, &chi2);
+            G.fit[slot0 + r] = make_float4(p[0], p[1], p[2], p[3]);
+            G.chi2[slot0 + r] = chi2;
+            st += nh;
         }
-    }
-    __syncthreads();
-    for (int k = tid; k < T; k += NT) {
-        uint32_t v = R.finals[k];
-        int q = (int)(v & 0xFFFF), nh = (int)(v >> 16);
-        const int r = R.fin_rank[k];
-        const int st = R.fin_start[r];
-        for (int j = nh - 1; j >= 0; j--) {
-            G.hits[(int64_t)off + st + j] = off + __float_as_int(R.coords[q].w);
-            pos[st + j] = (uint16_t)q;
-            q = R.prev[q];
-        }
-        float p[4], chi2;
-        fit_line(
-            nh,
-            [&](int i) {
-                float4 c = R.coords[pos[st + i]];
-                return make_float3(c.x, c.y, c.z);
-            },
-            C.sigma, p, &chi2);
-        G.fit[slot0 + r] = make_float4(p[0], p[1], p[2], p[3]);
-        G.chi2[slot0 + r] = chi2;
     }
     if (tid == 0) {
         G.ev_ntracks[e] = T;
