@@ -272,125 +272,82 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 
 // ------------------------------------------------------------- sorting ---
 
-constexpr int kSortThreads = 1024;
-constexpr int kSortWarps = 16;  // warps that build digit histograms and scatter (the rest wait)
+constexpr int kSortThreads = 512;
+constexpr int kSortBuckets = 4096;  // (module, top six bits of phi16)
+constexpr int kShortBucket = 8;     // buckets up to this size are sorted by one thread
 
-// Shared memory of the sort kernel: keys and indices ping-pong (12 B per hit)
-// and the per-warp digit histograms.
-__host__ __device__ inline size_t sort_layout(int nmax, size_t* off_kb, size_t* off_ia,
-                                              size_t* off_ib, size_t* off_hist, size_t* off_misc)
+// Shared memory of the sort kernel: the bucketed entries phi16 << 14 | input
+// index (4 B per hit), phi16 by input order (2 B per hit; later the list of
+// long buckets) and the bucket counters.
+__host__ __device__ inline size_t sort_layout(int nmax, size_t* off_phi, size_t* off_cnt)
 {
-    size_t o = 0;
-    const size_t ka = o;  o = align16(o + 4 * (size_t)nmax);
-    *off_kb = o;          o = align16(o + 4 * (size_t)nmax);
-    *off_ia = o;          o = align16(o + 2 * (size_t)nmax);
-    *off_ib = o;          o = align16(o + 2 * (size_t)nmax);
-    *off_hist = o;        o = align16(o + 4 * 256 * (size_t)kSortWarps);
-    *off_misc = o;        o = align16(o + 4 * (256 + 256 + 40 + kMiscN));
-    (void)ka;
+    size_t o = align16(4 * (size_t)nmax);
+    *off_phi = o;  o = align16(o + 2 * (size_t)nmax);
+    *off_cnt = o;  o = align16(o + 4 * (size_t)kSortBuckets);
     return o;
 }
 
 size_t sort_smem_bytes(int nmax)
 {
-    size_t a, b, c, d, e;
-    return sort_layout(nmax, &a, &b, &c, &d, &e);
+    size_t a, b;
+    return sort_layout(nmax, &a, &b);
 }
 
-// One stable counting pass over `bits` bits of the keys (key >> shift): the
-// keys travel with their indices.  Warp w owns the contiguous chunk w of the
-// input; ranks among equal digits inside a warp come from match/popc.
-__device__ void radix_pass(const uint32_t* ks, const uint16_t* is, uint32_t* kd, uint16_t* id,
-                           int n, int shift, int bits, int* hist, int* tot, int* base,
-                           int* modoff_out, int M)
+// Ascending sort of a[0, s) by one warp, in place: a bitonic network in the
+// form whose comparators all put the smaller key first (a mirrored merge
+// step, then half-cleaners), so positions past s behave as +infinity and are
+// never touched.
+__device__ void warp_bitonic(uint32_t* a, int s)
 {
-    constexpr int NT = kSortThreads, NW = kSortWarps;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nd = 1 << bits;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int k = tid; k < NW * 256; k += NT) hist[k] = 0;
-    __syncthreads();
-    const int chunk = (n + NW - 1) / NW;
-    const int beg = warp * chunk;
-    const int end = warp < NW ? min(n, beg + chunk) : 0;
-    for (int b = beg; b < end; b += 32) {
-        int j = b + lane;
-        bool v = j < end;
-        unsigned d = v ? ((ks[j] >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
-        unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-        if (v && lane == __ffs(peers) - 1) hist[warp * 256 + d] += __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int d = tid; d < nd; d += NT) {
-        int s = 0;
-        for (int w = 0; w < NW; w++) s += hist[w * 256 + d];
-        tot[d] = s;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int per = nd / 32;
-        int s = 0;
-        for (int k = 0; k < per; k++) s += tot[lane * per + k];
-        int incl = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int ex = incl - s;
-        for (int k = 0; k < per; k++) {
-            base[lane * per + k] = ex;
-            ex += tot[lane * per + k];
-        }
-    }
-    __syncthreads();
-    for (int d = tid; d < nd; d += NT) {
-        int b = base[d];
-        for (int w = 0; w < NW; w++) {
-            int h = hist[w * 256 + d];
-            hist[w * 256 + d] = b;
-            b += h;
-        }
-    }
-    if (modoff_out)
-        for (int d = tid; d <= M; d += NT) modoff_out[d] = d < M ? base[d] : n;
-    __syncthreads();
-    for (int b = beg; b < end; b += 32) {
-        int j = b + lane;
-        bool v = j < end;
-        uint32_t key = v ? ks[j] : 0u;
-        unsigned d = v ? ((key >> shift) & (unsigned)(nd - 1)) : 0xFFFFu;
-        unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-        int pos = v ? hist[warp * 256 + d] + __popc(peers & lt) : 0;
-        __syncwarp();
-        if (v) {
-            kd[pos] = key;
-            id[pos] = is[j];
-            if (lane == __ffs(peers) - 1) hist[warp * 256 + d] += __popc(peers);
+    const int lane = threadIdx.x & 31;
+    int P = 1;
+    while (P < s) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        const int h = k >> 1;
+        for (int i = lane; i < P / 2; i += 32) {
+            const int lo = (i / h) * k + (i % h), hi = (i / h) * k + k - 1 - (i % h);
+            if (hi < s) {
+                const uint32_t u = a[lo], v = a[hi];
+                if (u > v) {
+                    a[lo] = v;
+                    a[hi] = u;
+                }
+            }
         }
         __syncwarp();
+        for (int j = k >> 2; j >= 1; j >>= 1) {
+            for (int i = lane; i < P / 2; i += 32) {
+                const int lo = (i / j) * 2 * j + (i % j), hi = lo + j;
+                if (hi < s) {
+                    const uint32_t u = a[lo], v = a[hi];
+                    if (u > v) {
+                        a[lo] = v;
+                        a[hi] = u;
+                    }
+                }
+            }
+            __syncwarp();
+        }
     }
-    __syncthreads();
 }
 
 // One block per event: phi16, stable sort by (module, phi16) in shared
-// memory, gather of the sorted hits.  Status SBT_ERR_ARG for a module id out
-// of range, SBT_ERR_CAPACITY above the configured hit limit.
+// memory, gather of the sorted hits.  A counting pass puts every hit into its
+// (module, top six bits of phi16) bucket; each bucket is then sorted by
+// phi16 << 14 | input index, a unique key, so the order is the one of a
+// stable sort by (module, phi16).  Status SBT_ERR_ARG for a module id out of
+// range, SBT_ERR_CAPACITY above the configured hit limit.
 __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, Sorted O)
 {
+    constexpr int NT = kSortThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t okb, oia, oib, ohist, omisc;
-    sort_layout(C.nmax, &okb, &oia, &oib, &ohist, &omisc);
-    uint32_t* kA = (uint32_t*)smem_raw;
-    uint32_t* kB = (uint32_t*)(smem_raw + okb);
-    uint16_t* iA = (uint16_t*)(smem_raw + oia);
-    uint16_t* iB = (uint16_t*)(smem_raw + oib);
-    int* hist = (int*)(smem_raw + ohist);
-    int* tot = (int*)(smem_raw + omisc);
-    int* base = tot + 256;
-    int* misc = base + 256 + 40;
-    __shared__ int modoff[kMaxModules + 1];
+    size_t ophi, ocnt;
+    sort_layout(C.nmax, &ophi, &ocnt);
+    uint32_t* ent = (uint32_t*)smem_raw;
+    uint16_t* phi = (uint16_t*)(smem_raw + ophi);
+    int* cnt = (int*)(smem_raw + ocnt);
+    __shared__ int wsum[40];
+    __shared__ int err, nlong;
     const int tid = threadIdx.x;
     const int e = blockIdx.x;
     const int off = in.offsets[e];
@@ -399,15 +356,19 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
         if (tid == 0) O.status[e] = n < 0 ? SBT_ERR_ARG : SBT_ERR_CAPACITY;
         return;
     }
-    if (tid == 0) misc[kErr] = 0;
+    for (int b = tid; b < kSortBuckets; b += NT) cnt[b] = 0;
+    if (tid == 0) {
+        err = 0;
+        nlong = 0;
+    }
     __syncthreads();
-    // keys: four hits per thread per round, loads issued before use
-    for (int i0 = tid; i0 < n; i0 += 4 * kSortThreads) {
+    // phi16 and bucket counts, four hits per thread per round (loads first)
+    for (int i0 = tid; i0 < n; i0 += 4 * NT) {
         float xs[4], ys[4];
         int ms[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const int i = i0 + u * kSortThreads;
+            const int i = i0 + u * NT;
             const bool v = i < n;
             xs[u] = v ? in.x[off + i] : 1.0f;
             ys[u] = v ? in.y[off + i] : 0.0f;
@@ -415,46 +376,100 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const int i = i0 + u * kSortThreads;
+            const int i = i0 + u * NT;
             if (i >= n) continue;
             int m = ms[u];
             if (m < 0 || m >= C.M) {
-                misc[kErr] = SBT_ERR_ARG;
+                err = SBT_ERR_ARG;
                 m = 0;
             }
-            kA[i] = ((uint32_t)m << 16) | phi16_of(xs[u], ys[u]);
-            iA[i] = (uint16_t)i;
+            const uint32_t ph = phi16_of(xs[u], ys[u]);
+            phi[i] = (uint16_t)ph;
+            atomicAdd(&cnt[(m << 6) | (int)(ph >> 10)], 1);
         }
     }
     __syncthreads();
-    if (misc[kErr]) {
+    if (err) {
         if (tid == 0) O.status[e] = SBT_ERR_ARG;
         return;
     }
-    radix_pass(kA, iA, kB, iB, n, 0, 8, hist, tot, base, nullptr, C.M);
-    radix_pass(kB, iB, kA, iA, n, 8, 8, hist, tot, base, nullptr, C.M);
-    radix_pass(kA, iA, kB, iB, n, 16, 6, hist, tot, base, modoff, C.M);
+    // bucket starts: exclusive scan, kSortBuckets / NT consecutive buckets per thread
+    {
+        constexpr int per = kSortBuckets / NT;
+        int v[per];
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < per; k++) {
+            v[k] = cnt[tid * per + k];
+            s += v[k];
+        }
+        int total;
+        int st = block_exclusive_scan<NT>(s, wsum, &total);
+#pragma unroll
+        for (int k = 0; k < per; k++) {
+            cnt[tid * per + k] = st;
+            st += v[k];
+        }
+    }
+    __syncthreads();
+    // scatter into the buckets (order inside a bucket arbitrary); afterwards
+    // cnt[b] is the end of bucket b
+    for (int i = tid; i < n; i += NT) {
+        const uint32_t ph = phi[i];
+        const int m = in.module[off + i];
+        const int p = atomicAdd(&cnt[(m << 6) | (int)(ph >> 10)], 1);
+        ent[p] = (ph << 14) | (uint32_t)i;
+    }
+    __syncthreads();
+    // short buckets: insertion sort by one thread; long ones listed for a warp
+    uint16_t* longb = phi;  // phi16 by input order is no longer needed
+    for (int b = tid; b < kSortBuckets; b += NT) {
+        const int lo = b > 0 ? cnt[b - 1] : 0, hi = cnt[b];
+        if (hi - lo > kShortBucket) {
+            longb[atomicAdd(&nlong, 1)] = (uint16_t)b;
+            continue;
+        }
+        for (int k = lo + 1; k < hi; k++) {
+            const uint32_t v = ent[k];
+            int j = k - 1;
+            while (j >= lo && ent[j] > v) {
+                ent[j + 1] = ent[j];
+                j--;
+            }
+            ent[j + 1] = v;
+        }
+    }
+    __syncthreads();
+    for (int q = tid >> 5; q < nlong; q += NT / 32) {
+        const int b = longb[q];
+        const int lo = b > 0 ? cnt[b - 1] : 0;
+        warp_bitonic(ent + lo, cnt[b] - lo);
+    }
+    for (int m = tid; m <= C.M; m += NT)
+        O.modoff[(int64_t)e * (C.M + 1) + m] = m == 0 ? 0 : (m < C.M ? cnt[(m << 6) - 1] : n);
+    __syncthreads();
     // gather of the sorted hits, four per thread per round
-    for (int p0 = tid; p0 < n; p0 += 4 * kSortThreads) {
+    for (int p0 = tid; p0 < n; p0 += 4 * NT) {
         float4 c[4];
+        uint32_t en[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const int p = p0 + u * kSortThreads;
+            const int p = p0 + u * NT;
             if (p < n) {
-                const int i = iB[p];
+                en[u] = ent[p];
+                const int i = (int)(en[u] & 0x3FFFu);
                 c[u] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
             }
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const int p = p0 + u * kSortThreads;
+            const int p = p0 + u * NT;
             if (p < n) {
-                O.phi[off + p] = (uint16_t)(kB[p] & 0xFFFFu);
+                O.phi[off + p] = (uint16_t)(en[u] >> 14);
                 O.coords[off + p] = c[u];
             }
         }
     }
-    for (int m = tid; m <= C.M; m += kSortThreads) O.modoff[(int64_t)e * (C.M + 1) + m] = modoff[m];
     if (tid == 0) O.status[e] = SBT_OK;
 }
 

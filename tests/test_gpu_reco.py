@@ -97,6 +97,39 @@ def test_sort_stage_bit_exact(sbt, handle):
         assert np.array_equal(mo[e], o)
 
 
+def test_sort_crowded_buckets_bit_exact(sbt):
+    """Sort parity where (module, coarse phi) buckets hold many hits: equal
+    phi16 values (order by input index), a dense phi band, and a sparse rest."""
+    rng = np.random.default_rng(5)
+    parts = []
+    # 3000 hits at one point (identical phi16), 2500 in a narrow phi band,
+    # 40 alone in their buckets, all on modules 3 and 7, plus a sparse spread
+    parts.append((np.full(3000, 7.0), np.full(3000, 2.0), np.full(3000, 3)))
+    ang = rng.uniform(0.30, 0.32, 2500)
+    parts.append((10 * np.cos(ang), 10 * np.sin(ang), np.full(2500, 7)))
+    ang = np.linspace(-3.1, 3.1, 40)
+    parts.append((20 * np.cos(ang), 20 * np.sin(ang), np.full(40, 3)))
+    ang = rng.uniform(-np.pi, np.pi, 900)
+    parts.append((15 * np.cos(ang), 15 * np.sin(ang), rng.integers(0, 52, 900)))
+    x = np.concatenate([p[0] for p in parts]).astype(np.float32)
+    y = np.concatenate([p[1] for p in parts]).astype(np.float32)
+    m = np.concatenate([p[2] for p in parts]).astype(np.int32)
+    perm0 = rng.permutation(len(x))
+    x, y, m = x[perm0], y[perm0], m[perm0]
+    z = MZ[m].astype(np.float32)
+    ev = arrays(x, y, z, m)
+    h = sbt.sbt_create(MZ, sbt.default_config(max_hits_per_event=8192, **CFG))
+    try:
+        phi, perm, mo = sbt.sbt_debug_sort(h, *[to_dev(ev)[i] for i in (0, 1, 3, 4)])
+        torch.cuda.synchronize()
+    finally:
+        h.close()
+    p, o, ph = oracle.sort_event(ev.x, ev.y, ev.module, 52)
+    assert np.array_equal(perm.cpu().numpy(), p)
+    assert np.array_equal(phi.cpu().numpy().view(np.uint16), ph)
+    assert np.array_equal(mo.cpu().numpy()[0], o)
+
+
 @pytest.mark.parametrize("batched", [False, True])
 def test_small_workload_bit_exact(sbt, handle, batched):
     ev = synth.make_events(1, workers=1)
