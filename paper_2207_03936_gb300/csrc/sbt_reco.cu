@@ -274,7 +274,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 
 constexpr int kSortThreads = 512;
 constexpr int kSortBuckets = 4096;  // (module, top six bits of phi16)
-constexpr int kShortBucket = 8;     // buckets up to this size are sorted by one thread
+constexpr int kShortBucket = 32;    // buckets up to this size are sorted by one thread
 
 // Shared memory of the sort kernel: the bucketed entries phi16 << 14 | input
 // index (4 B per hit), phi16 by input order (2 B per hit; later the list of
