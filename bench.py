@@ -16,6 +16,7 @@ collective on the data path) and rank 0 prints the JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -56,6 +57,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def profiled_traffic(kernel, hits):
+    """DRAM bytes of one launch of `kernel` over `hits` hits, scaled from the
+    committed ncu capture (bytes per hit); None once the kernel source differs
+    from the one the counters were taken on."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    with open(os.path.join(ROOT, d["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != d["source_sha256"]:
+            return None
+    k = d["kernels"].get(kernel)
+    if k is None:
+        return None
+    return (k["dram_read_bytes"] + k["dram_write_bytes"]) / k["hits"] * hits
 
 
 def peaks():
@@ -365,11 +384,15 @@ def main():
             "adjoint": adj,
             "e2e": e2e,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": profiled_traffic("k_search_persistent", ev.n_hits),
+                         "traffic_source": "ncu capture of 4000 events scaled per hit",
+                         "peak_kind": peak_kind,
                          "kernel": "k_search_persistent", "kernel_ms": kms[2],
                          "kernel_ms_all": {"order": kms[0], "sort": kms[1], "search": kms[2],
                                            "scan": kms[3], "consolidate": kms[4]},
-                         "sort_kernel": {"achieved_gbs": sort_gbs, "frac": sort_gbs / peak}},
+                         "sort_kernel": {"achieved_gbs": sort_gbs, "frac": sort_gbs / peak,
+                                         "traffic": profiled_traffic("k_sort", ev.n_hits)}},
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clk,
