@@ -19,8 +19,14 @@ namespace {
 std::string g_create_error;
 
 // Host pipeline: events per chunk and the most chunks per call.
+// Host pipeline: batches above kChunkEvents events are cut into chunks of
+// relative sizes kChunkWeights (small first chunk: short start-up; sizes
+// growing by at most 1.6x: the next upload, at about 0.6 of the compute time
+// per event, stays hidden; smaller last chunks: short download at the end).
 constexpr int64_t kChunkEvents = 12500;
 constexpr int kMaxChunks = 16;
+constexpr double kChunkWeights[] = {1.0, 1.6, 2.6, 4.1, 6.6, 10.5, 16.8, 8.0, 3.0};
+constexpr int kWeightedChunks = sizeof(kChunkWeights) / sizeof(kChunkWeights[0]);
 
 // One device allocation carved into aligned sub-arrays.
 struct Arena {
@@ -464,9 +470,17 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     // chunks of whole events: inputs of chunk c+1 upload while chunk c
     // computes, results of chunk c download while chunk c+1 computes
     const int64_t H = n_hits, E = n_events;
-    const int C = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, (E + kChunkEvents - 1) / kChunkEvents));
+    const int C = E > kChunkEvents ? kWeightedChunks : 1;
     std::vector<int32_t> e0(C + 1);
-    for (int c = 0; c <= C; c++) e0[c] = (int32_t)((E * c) / C);
+    {
+        double wsum = 0.0, acc = 0.0;
+        for (int c = 0; c < C; c++) wsum += C > 1 ? kChunkWeights[c] : 1.0;
+        e0[0] = 0;
+        for (int c = 0; c < C; c++) {
+            acc += C > 1 ? kChunkWeights[c] : 1.0;
+            e0[c + 1] = c + 1 == C ? (int32_t)E : (int32_t)((double)E * acc / wsum);
+        }
+    }
     auto layout = [&](Carver& cv, float** dx, float** dy, float** dz, int32_t** dm, int32_t** doff,
                       int32_t** dto, int32_t** dho, int32_t** dth, float** dpar, float** dchi,
                       int32_t** dndof, int32_t** dstat, int32_t** dcnt, int64_t** drun) {

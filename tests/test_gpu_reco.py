@@ -305,6 +305,38 @@ def test_host_entry_point_matches_device(sbt, handle):
     assert np.array_equal(out.params[:4 * T].numpy().reshape(T, 4), o.params)
 
 
+def test_host_entry_point_chunked_matches_device(sbt):
+    """Above 12500 events the host entry point cuts the batch into chunks of
+    uneven size (uploads, reconstruction and downloads overlapped); the result
+    must equal the one-call device path, hit indices and offsets global."""
+    ev = synth.make_events(1, 20000, workers=1)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(**CFG))
+    try:
+        d = sbt.sbt_reconstruct_batched(h, *to_dev(ev))
+        torch.cuda.synchronize()
+        g = d.compact()
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        out = sbt.sbt_reconstruct_host(h, pin(ev.x), pin(ev.y), pin(ev.z), pin(ev.module),
+                                       pin(ev.event_offsets))
+    finally:
+        h.close()
+    T, H = int(out.counts[0]), int(out.counts[1])
+    assert T == len(g["ndof"]) and H == len(g["track_hits"])
+    assert np.array_equal(out.event_status.numpy(), g["event_status"])
+    assert np.array_equal(out.track_offsets.numpy(), g["track_offsets"])
+    assert np.array_equal(out.hit_offsets[:T + 1].numpy(), g["hit_offsets"])
+    assert np.array_equal(out.track_hits[:H].numpy(), g["track_hits"])
+    assert np.array_equal(out.params[:4 * T].numpy().view(np.uint32), g["params"].reshape(-1).view(np.uint32))
+    assert np.array_equal(out.chi2[:T].numpy().view(np.uint32), g["chi2"].view(np.uint32))
+    assert np.array_equal(out.ndof[:T].numpy(), g["ndof"])
+    # and a sample of events against the oracle
+    o = oracle.reconstruct(ev.x[:ev.event_offsets[200]], ev.y[:ev.event_offsets[200]],
+                           ev.z[:ev.event_offsets[200]], ev.module[:ev.event_offsets[200]],
+                           ev.event_offsets[:201], ev.module_z, oracle.config(**CFG))
+    assert np.array_equal(out.track_offsets.numpy()[:201], o.track_offsets)
+    assert np.array_equal(out.track_hits[:len(o.track_hits)].numpy(), o.track_hits)
+
+
 def test_autotune_keeps_results(sbt):
     ev = synth.make_events(2, 300, workers=1)
     h = sbt.sbt_create(MZ, sbt.default_config(**CFG))
