@@ -4,8 +4,9 @@ A step reconstructs one batch of synthetic events (100k uneven events, pileup
 U(1, 20), 200-12600 hits each; inputs larger than L2) through the batched C
 entry point (persistent work-queue kernel replayed from a CUDA graph).  The
 line also reports the plain one-block-per-event launch on the same batch,
-the end-to-end host entry point (copies inside the timed region), the
-alignment adjoint, the dominant kernel's roofline fraction, the SM clocks
+the same batch traversed in ascending z (module order reversed), the
+end-to-end host entry point (copies inside the timed region), the alignment
+adjoint, the dominant kernel's roofline fraction, the SM clocks
 seen during the timed region and the CPU oracle timed on host cores over a
 bounded sample, whose tracks are compared with the GPU's event by event.
 
@@ -47,6 +48,8 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-direction", action="store_true",
+                   help="skip the ascending-z traversal of the same batch")
     p.add_argument("--serving-sweep", action="store_true",
                    help="sweep arrival rate (0.1-1.5x of saturation) and memory budget (2-16 GB)")
     return p.parse_args()
@@ -322,6 +325,30 @@ def main():
                  "identical_to_batched": bool(same)}
         del pout
 
+    # the same batch traversed in ascending z: module ids and planes reversed
+    ascending = None
+    if not args.no_direction:
+        M = len(ev.module_z)
+        dev_asc = list(dev)
+        dev_asc[3] = (M - 1 - dev[3]).to(torch.int32)
+        ha = sbt.sbt_create(ev.module_z[::-1].copy(),
+                            sbt.default_config(max_hits_per_event=nmax, threads_per_block=threads))
+        aout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
+        for _ in range(max(1, min(args.warmup, 2))):
+            sbt.sbt_reconstruct_batched(ha, *dev_asc, out=aout)
+        torch.cuda.synchronize()
+        n_asc = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(n_asc):
+            sbt.sbt_reconstruct_batched(ha, *dev_asc, out=aout)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ams = a.elapsed_time(b) / n_asc
+        ascending = {"value": ev.n_events / (ams / 1e3), "unit": "events/s", "ms_per_step": ams,
+                     "tracks": int(aout.counts[0].item()), "tracks_descending": T}
+        ha.close()
+        del aout, dev_asc
+
     # end to end through the host entry point (pinned host buffers)
     host_in = [torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
     hout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, pin_memory=True)
@@ -379,6 +406,7 @@ def main():
                        "tracks": T, "threads_per_block": threads,
                        "l2": "inputs larger than L2 (no flush needed)"},
             "plain": plain,
+            "ascending": ascending,
             "serving": serving,
             "match": match,
             "adjoint": adj,

@@ -324,6 +324,15 @@ def make_events(config: int, n_events: int | None = None, seed: int = 0,
     return generate(recipe_for(config, n_events, seed), workers)
 
 
+def reverse_traversal(ev: Events) -> Events:
+    """The same hits traversed in the opposite direction (ascending z, from
+    behind the interaction region outwards): module id m becomes M - 1 - m
+    and the plane positions are reversed."""
+    M = int(ev.module_z.shape[0])
+    return Events(ev.x, ev.y, ev.z, (M - 1 - ev.module).astype(np.int32), ev.event_offsets, ev.mc,
+                  ev.n_particles, ev.module_z[::-1].copy())
+
+
 def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:
     """Open-loop arrival times (seconds from 0) of n requests at a mean rate."""
     rng = np.random.Generator(np.random.PCG64([seed, 0xA77]))

@@ -142,6 +142,20 @@ def test_upgrade_workload_bit_exact(sbt, handle, batched):
     assert_same(run_gpu(sbt, handle, ev, batched), oracle_of(ev))
 
 
+@pytest.mark.parametrize("config,n", [(2, 300), (3, 150)])
+def test_ascending_traversal_bit_exact(sbt, config, n):
+    """Traversal in ascending z (module ids and plane positions reversed):
+    the same kernels, plain and batched, against the oracle."""
+    ev = synth.reverse_traversal(synth.make_events(config, n))
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(**CFG))
+    try:
+        o = oracle_of(ev)
+        assert_same(run_gpu(sbt, h, ev, False), o)
+        assert_same(run_gpu(sbt, h, ev, True), o)
+    finally:
+        h.close()
+
+
 def test_uneven_workload_bit_exact(sbt, handle):
     ev = synth.make_events(3, 400)
     o = oracle_of(ev)

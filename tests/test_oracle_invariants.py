@@ -69,6 +69,31 @@ def test_physics_indicators_against_truth(config):
     assert ind["hit_efficiency"] >= 0.98
 
 
+@pytest.mark.parametrize("config,n", [(2, 150), (3, 30)])
+def test_invariants_ascending_traversal(config, n):
+    """The same hits traversed in ascending z (module ids reversed): the
+    track invariants hold in the new module order."""
+    ev = synth.reverse_traversal(synth.make_events(config, n, workers=1))
+    res = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                             oracle.config(**CFG))
+    assert (res.status == 0).all()
+    check_invariants(ev, res, CFG)
+
+
+@pytest.mark.parametrize("config", [1, 2])
+def test_physics_indicators_ascending_traversal(config):
+    # same thresholds as the descending traversal
+    ev = synth.reverse_traversal(synth.make_events(config, workers=1))
+    res = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                             oracle.config(**CFG))
+    ind = validation.indicators(res.hit_offsets, res.track_hits, ev.mc, ev.n_particles)
+    assert ind["efficiency"] >= 0.995
+    assert ind["fake_fraction"] <= 0.005
+    assert ind["clone_fraction"] <= 0.015
+    assert ind["hit_purity"] >= 0.995
+    assert ind["hit_efficiency"] >= 0.98
+
+
 def test_batch_equals_single_event_calls():
     ev = synth.make_events(2, 25, workers=1)
     res = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
