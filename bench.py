@@ -4,7 +4,8 @@ A step reconstructs one batch of synthetic events (100k uneven events, pileup
 U(1, 20), 200-12600 hits each; inputs larger than L2) through the batched C
 entry point (persistent work-queue kernel replayed from a CUDA graph).  The
 line also reports the plain one-block-per-event launch on the same batch,
-the same batch traversed in ascending z (module order reversed), the
+the same batch traversed in ascending z (module order reversed) and with the
+global event cut (busiest 10% of events rejected), the
 end-to-end host entry point (copies inside the timed region), the alignment
 adjoint, the dominant kernel's roofline fraction, the SM clocks
 seen during the timed region and the CPU oracle timed on host cores over a
@@ -50,6 +51,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-direction", action="store_true",
                    help="skip the ascending-z traversal of the same batch")
+    p.add_argument("--no-gec", action="store_true",
+                   help="skip the global-event-cut run (busiest 10% of events rejected)")
     p.add_argument("--serving-sweep", action="store_true",
                    help="sweep arrival rate (0.1-1.5x of saturation) and memory budget (2-16 GB)")
     return p.parse_args()
@@ -349,6 +352,47 @@ def main():
         ha.close()
         del aout, dev_asc
 
+    # global event cut: the busiest 10% of events rejected unreconstructed;
+    # throughput over all input events, physics traded on a truth sample
+    gec = None
+    if not args.no_gec:
+        from paper_2207_03936_gb300 import validation
+        sizes = np.diff(ev.event_offsets)
+        thr = int(np.quantile(sizes, 0.9))
+        hg = sbt.sbt_create(ev.module_z, sbt.default_config(max_hits_per_event=nmax, threads_per_block=threads,
+                                                            gec_max_hits=thr))
+        gout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
+        for _ in range(max(1, min(args.warmup, 2))):
+            sbt.sbt_reconstruct_batched(hg, *dev, out=gout)
+        torch.cuda.synchronize()
+        n_gec = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(n_gec):
+            sbt.sbt_reconstruct_batched(hg, *dev, out=gout)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gms = a.elapsed_time(b) / n_gec
+        K = min(2000, ev.n_events)
+
+        def sample_indicators(res):
+            to, ho = res["track_offsets"], res["hit_offsets"]
+            tk = int(to[K])
+            return validation.indicators(ho[:tk + 1], res["track_hits"][:int(ho[tk])],
+                                         ev.mc[:int(ev.event_offsets[K])], ev.n_particles)
+        gres = gout.compact()
+        base_ind, cut_ind = sample_indicators(gpu_res), sample_indicators(gres)
+        keep = sizes <= thr
+        gec = {"max_hits": thr, "kept_events": int(keep.sum()),
+               "kept_hits_fraction": float(sizes[keep].sum() / sizes.sum()),
+               "value": ev.n_events / (gms / 1e3), "unit": "input events/s", "ms_per_step": gms,
+               "speedup": ms / gms, "tracks": int(gres["counts"][0]),
+               "sample": {"events": K, "efficiency_without_cut": base_ind["efficiency"],
+                          "efficiency_with_cut": cut_ind["efficiency"],
+                          "fake_fraction_with_cut": cut_ind["fake_fraction"],
+                          "clone_fraction_with_cut": cut_ind["clone_fraction"]}}
+        hg.close()
+        del gout, gres
+
     # end to end through the host entry point (pinned host buffers)
     host_in = [torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
     hout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, pin_memory=True)
@@ -407,6 +451,7 @@ def main():
                        "l2": "inputs larger than L2 (no flush needed)"},
             "plain": plain,
             "ascending": ascending,
+            "gec": gec,
             "serving": serving,
             "match": match,
             "adjoint": adj,

@@ -43,7 +43,8 @@ typedef enum {
     SBT_ERR_CAPACITY = 2, /* output or per-event capacity exceeded (device-reported) */
     SBT_ERR_CUDA = 3,     /* CUDA runtime error; see sbt_last_error */
     SBT_ERR_TIMEOUT = 4,  /* a bounded wait expired (serving) */
-    SBT_ERR_STATE = 5     /* call not valid in the object's current state */
+    SBT_ERR_STATE = 5,    /* call not valid in the object's current state */
+    SBT_EVENT_CUT = 6     /* per-event only: rejected by the global event cut, no tracks */
 } sbt_status;
 
 typedef struct sbt_handle sbt_handle;
@@ -69,6 +70,9 @@ typedef struct {
     int32_t max_hits_per_event;  /* events with more hits get SBT_ERR_CAPACITY; default and maximum 16384 */
     int32_t max_forming_tracks;  /* forming tracks alive per event: n_hits/12 + 64; a positive value lowers the bound */
     int32_t threads_per_block;   /* 64, 128 or 256; 0 = 128 (batched: autotuned value if any) */
+    int32_t gec_max_hits;        /* global event cut (the paper's VELO sequence, first step): events
+                                    with more hits are rejected unreconstructed (event status
+                                    SBT_EVENT_CUT); 0 = no cut (default) */
 } sbt_config;
 
 /* Reconstructed tracks, CSR over events and tracks.  All arrays are device
@@ -81,13 +85,14 @@ typedef struct {
  *   params        [cap_tracks * 4] x0, y0, tx, ty of x = x0 + tx z, y = y0 + ty z
  *   chi2          [cap_tracks]     sum of squared residuals / hit_sigma^2
  *   ndof          [cap_tracks]     2 * hits - 4
- *   event_status  [n_events]       SBT_OK, SBT_ERR_ARG (module id out of range) or
+ *   event_status  [n_events]       SBT_OK, SBT_ERR_ARG (module id out of range),
  *                                  SBT_ERR_CAPACITY (event above max_hits_per_event
- *                                  or a per-event buffer full); failed events have no tracks
+ *                                  or a per-event buffer full) or SBT_EVENT_CUT (above
+ *                                  gec_max_hits); failed and cut events have no tracks
  *   counts        [4]              required tracks, required track hits, SBT_OK or
  *                                  SBT_ERR_CAPACITY when cap_* was too small (then
  *                                  nothing beyond the capacities is written), number
- *                                  of failed events
+ *                                  of failed events (cut events not included)
  * Tracks of an event are ordered by their smallest hit index. */
 typedef struct {
     int32_t* track_offsets;

@@ -281,6 +281,7 @@ sbt_status sbt_default_config(sbt_config* out)
     out->max_hits_per_event = 16384;
     out->max_forming_tracks = 0;
     out->threads_per_block = 0;
+    out->gec_max_hits = 0;
     return SBT_OK;
 }
 
@@ -301,7 +302,7 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
     else
         sbt_default_config(&c);
     if (c.k_doublets < 1 || c.max_hits_per_event < 1 || c.max_hits_per_event > kMaxHitsPerEvent ||
-        c.max_forming_tracks < 0 || !(c.hit_sigma > 0.0f) ||
+        c.max_forming_tracks < 0 || c.gec_max_hits < 0 || !(c.hit_sigma > 0.0f) ||
         (c.threads_per_block != 0 && c.threads_per_block != 64 && c.threads_per_block != 128 &&
          c.threads_per_block != 256)) {
         g_create_error = "invalid configuration";
@@ -319,6 +320,7 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
     h->C.sigma = c.hit_sigma;
     h->C.nmax = c.max_hits_per_event;
     h->C.fcap = c.max_forming_tracks;
+    h->C.gec = c.gec_max_hits;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);

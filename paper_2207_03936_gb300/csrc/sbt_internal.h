@@ -20,6 +20,7 @@ struct DevConfig {
     float S_seed, S_follow, C3, sigma;
     int nmax;  // max hits per event
     int fcap;  // upper bound on forming tracks per event (0: forming_capacity(n) only)
+    int gec;   // global event cut: events above this many hits are rejected (0: none)
 };
 
 struct Inputs {

@@ -352,8 +352,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
-    if (n < 0 || n > C.nmax) {
-        if (tid == 0) O.status[e] = n < 0 ? SBT_ERR_ARG : SBT_ERR_CAPACITY;
+    if (n < 0 || n > C.nmax || (C.gec > 0 && n > C.gec)) {
+        if (tid == 0)
+            O.status[e] = n < 0 ? SBT_ERR_ARG : (C.gec > 0 && n > C.gec) ? SBT_EVENT_CUT : SBT_ERR_CAPACITY;
         return;
     }
     for (int b = tid; b < kSortBuckets; b += NT) cnt[b] = 0;
@@ -1185,7 +1186,7 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
     for (int e = beg; e < end; e++) {
         t += G.ev_ntracks[e];
         h += G.ev_nhits[e];
-        f += out.event_status[e] != SBT_OK;
+        f += out.event_status[e] != SBT_OK && out.event_status[e] != SBT_EVENT_CUT;
     }
     int T, H, F;
     int bt = block_exclusive_scan<1024>(t, wsum, &T);

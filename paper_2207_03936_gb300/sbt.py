@@ -14,9 +14,10 @@ import torch
 
 from .build import LIB
 
-SBT_OK, SBT_ERR_ARG, SBT_ERR_CAPACITY, SBT_ERR_CUDA, SBT_ERR_TIMEOUT, SBT_ERR_STATE = range(6)
+SBT_OK, SBT_ERR_ARG, SBT_ERR_CAPACITY, SBT_ERR_CUDA, SBT_ERR_TIMEOUT, SBT_ERR_STATE, SBT_EVENT_CUT = range(7)
 _STATUS = {0: "SBT_OK", 1: "SBT_ERR_ARG", 2: "SBT_ERR_CAPACITY", 3: "SBT_ERR_CUDA",
-           4: "SBT_ERR_TIMEOUT", 5: "SBT_ERR_STATE"}
+           4: "SBT_ERR_TIMEOUT", 5: "SBT_ERR_STATE",
+           6: "SBT_EVENT_CUT"}
 
 
 class SbtError(RuntimeError):
@@ -34,7 +35,8 @@ class Config(ctypes.Structure):
     _fields_ = [("k_doublets", ctypes.c_int32), ("max_scatter_seed", ctypes.c_float),
                 ("max_scatter_follow", ctypes.c_float), ("max_chi2_tracklet", ctypes.c_float),
                 ("hit_sigma", ctypes.c_float), ("max_hits_per_event", ctypes.c_int32),
-                ("max_forming_tracks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32)]
+                ("max_forming_tracks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("gec_max_hits", ctypes.c_int32)]
 
 
 class TracksC(ctypes.Structure):

@@ -156,6 +156,44 @@ def test_ascending_traversal_bit_exact(sbt, config, n):
         h.close()
 
 
+def oracle_without(o, keep):
+    """The oracle's CSR tracks with the events where keep is False emptied."""
+    to, ho = o.track_offsets, o.hit_offsets
+    tracks = np.concatenate([np.arange(to[e], to[e + 1]) for e in range(len(keep)) if keep[e]]
+                            + [np.zeros(0, np.int64)]).astype(np.int64)
+    lens = ho[tracks + 1] - ho[tracks]
+    hits = np.concatenate([o.track_hits[ho[t]:ho[t + 1]] for t in tracks] + [np.zeros(0, np.int32)])
+    per_event = np.array([(to[e + 1] - to[e]) if keep[e] else 0 for e in range(len(keep))])
+    return dict(track_offsets=np.concatenate([[0], np.cumsum(per_event)]).astype(np.int32),
+                hit_offsets=np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                track_hits=hits.astype(np.int32), params=o.params[tracks], chi2=o.chi2[tracks],
+                ndof=o.ndof[tracks])
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_global_event_cut(sbt, batched):
+    """Events above gec_max_hits are rejected (status SBT_EVENT_CUT, no tracks,
+    not counted as failed); every other event is reconstructed exactly as
+    without the cut."""
+    ev = synth.make_events(3, 200)
+    sizes = np.diff(ev.event_offsets)
+    thr = int(np.quantile(sizes, 0.9))
+    keep = sizes <= thr
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(gec_max_hits=thr, **CFG))
+    try:
+        g = run_gpu(sbt, h, ev, batched)
+    finally:
+        h.close()
+    assert (g["event_status"][~keep] == sbt.SBT_EVENT_CUT).all()
+    assert (g["event_status"][keep] == sbt.SBT_OK).all()
+    assert int(g["counts"][3]) == 0 and int(g["counts"][2]) == 0
+    want = oracle_without(oracle_of(ev), keep)
+    for k in ("track_offsets", "hit_offsets", "track_hits", "ndof"):
+        assert np.array_equal(g[k], want[k]), k
+    assert np.array_equal(g["params"].view(np.uint32), want["params"].view(np.uint32))
+    assert np.array_equal(g["chi2"].view(np.uint32), want["chi2"].view(np.uint32))
+
+
 def test_uneven_workload_bit_exact(sbt, handle):
     ev = synth.make_events(3, 400)
     o = oracle_of(ev)
