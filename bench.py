@@ -5,7 +5,8 @@ U(1, 20), 200-12600 hits each; inputs larger than L2) through the batched C
 entry point (persistent work-queue kernel replayed from a CUDA graph).  The
 line also reports the plain one-block-per-event launch on the same batch,
 the same batch traversed in ascending z (module order reversed) and with the
-global event cut (busiest 10% of events rejected), the
+global event cut (busiest 10% of events rejected) and with fp16 hit
+storage, the
 end-to-end host entry point (copies inside the timed region), the alignment
 adjoint, the dominant kernel's roofline fraction, the SM clocks
 seen during the timed region and the CPU oracle timed on host cores over a
@@ -51,6 +52,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-direction", action="store_true",
                    help="skip the ascending-z traversal of the same batch")
+    p.add_argument("--no-fp16", action="store_true",
+                   help="skip the fp16 hit-storage run of the same batch")
     p.add_argument("--no-gec", action="store_true",
                    help="skip the global-event-cut run (busiest 10% of events rejected)")
     p.add_argument("--serving-sweep", action="store_true",
@@ -352,6 +355,29 @@ def main():
         ha.close()
         del aout, dev_asc
 
+    # fp16 hit storage (x, y, z rounded to fp16, 8 bytes per sorted hit)
+    fp16 = None
+    if not args.no_fp16:
+        hh = sbt.sbt_create(ev.module_z, sbt.default_config(max_hits_per_event=nmax, threads_per_block=threads,
+                                                            fp16_hits=1))
+        hout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
+        for _ in range(max(1, min(args.warmup, 2))):
+            sbt.sbt_reconstruct_batched(hh, *dev, out=hout)
+        torch.cuda.synchronize()
+        n_h = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(n_h):
+            sbt.sbt_reconstruct_batched(hh, *dev, out=hout)
+        b.record(stream)
+        torch.cuda.synchronize()
+        hms = a.elapsed_time(b) / n_h
+        hk = sbt.sbt_profile_batched(hh, *dev, hout, reps=2)
+        fp16 = {"value": ev.n_events / (hms / 1e3), "unit": "events/s", "ms_per_step": hms,
+                "speedup": ms / hms, "tracks": int(hout.counts[0].item()), "tracks_fp32": T,
+                "kernel_ms": {"sort": hk[1], "search": hk[2]}}
+        hh.close()
+        del hout
+
     # global event cut: the busiest 10% of events rejected unreconstructed;
     # throughput over all input events, physics traded on a truth sample
     gec = None
@@ -452,6 +478,7 @@ def main():
             "plain": plain,
             "ascending": ascending,
             "gec": gec,
+            "fp16_hits": fp16,
             "serving": serving,
             "match": match,
             "adjoint": adj,

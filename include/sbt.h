@@ -73,6 +73,10 @@ typedef struct {
     int32_t gec_max_hits;        /* global event cut (the paper's VELO sequence, first step): events
                                     with more hits are rejected unreconstructed (event status
                                     SBT_EVENT_CUT); 0 = no cut (default) */
+    int32_t fp16_hits;           /* 1: the sorted hits keep x, y, z rounded to fp16 (nearest even)
+                                    and a 16-bit index, 8 bytes per hit instead of 16 (the paper's
+                                    fp16 AoS hit storage); every computation stays fp32, on the
+                                    rounded coordinates, phi16 included.  0 = fp32 (default) */
 } sbt_config;
 
 /* Reconstructed tracks, CSR over events and tracks.  All arrays are device

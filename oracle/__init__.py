@@ -185,11 +185,22 @@ def event(x, y, z, module, module_z, cfg: Config | None = None):
                   c2[:nt].copy(), nd[:nt].copy(), np.zeros(1, np.int32), st.reshape(1, 8))
 
 
+def round_fp16(a) -> np.ndarray:
+    """fp32 values rounded to the nearest fp16 (ties to even) and back: the
+    coordinates of the fp16 hit-storage mode (the paper stores VELO hit
+    coordinates in 16-bit floats; its optimisation table, 05-03-2020)."""
+    return _f32(a).astype(np.float16).astype(np.float32)
+
+
 def reconstruct(x, y, z, module, event_offsets, module_z, cfg: Config | None = None,
-                n_threads: int | None = None) -> Tracks:
-    """Reconstruct a batch of events on host threads; returns CSR tracks."""
+                n_threads: int | None = None, fp16_hits: bool = False) -> Tracks:
+    """Reconstruct a batch of events on host threads; returns CSR tracks.
+    With fp16_hits the hit coordinates are first rounded to fp16, as the
+    fp16 hit-storage mode keeps them; everything after is unchanged."""
     cfg = cfg or config()
     x, y, z, module = _f32(x), _f32(y), _f32(z), _i32(module)
+    if fp16_hits:
+        x, y, z = round_fp16(x), round_fp16(y), round_fp16(z)
     eo, module_z = _i32(event_offsets), _f32(module_z)
     E = eo.shape[0] - 1
     H = int(eo[-1]) if E >= 0 else 0

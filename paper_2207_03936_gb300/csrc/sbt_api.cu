@@ -282,6 +282,7 @@ sbt_status sbt_default_config(sbt_config* out)
     out->max_forming_tracks = 0;
     out->threads_per_block = 0;
     out->gec_max_hits = 0;
+    out->fp16_hits = 0;
     return SBT_OK;
 }
 
@@ -321,6 +322,7 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
     h->C.nmax = c.max_hits_per_event;
     h->C.fcap = c.max_forming_tracks;
     h->C.gec = c.gec_max_hits;
+    h->C.h16 = c.fp16_hits ? 1 : 0;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);

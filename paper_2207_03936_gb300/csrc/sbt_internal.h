@@ -21,6 +21,7 @@ struct DevConfig {
     int nmax;  // max hits per event
     int fcap;  // upper bound on forming tracks per event (0: forming_capacity(n) only)
     int gec;   // global event cut: events above this many hits are rejected (0: none)
+    int h16;   // sorted hits stored as fp16 x, y, z + 16-bit index (8 bytes) instead of float4
 };
 
 struct Inputs {

@@ -19,6 +19,7 @@
 // Decision arithmetic is fp32 with every operation rounded as written
 // (explicit _rn intrinsics, no contraction), so that the result is the
 // exact track set of the plain definition.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -197,9 +198,44 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
 __device__ __forceinline__ bool flagged(const Smem& S, int p) { return (S.flag[p >> 5] >> (p & 31)) & 1u; }
 __device__ __forceinline__ void set_flag(const Smem& S, int p) { atomicOr(&S.flag[p >> 5], 1u << (p & 31)); }
 
+// Storage of the sorted hits.  HitsF32: float4 (x, y, z, input index as
+// int bits), 16 bytes.  HitsF16: x, y, z rounded to fp16 (nearest even) and
+// the input index in 16 bits, 8 bytes (the paper's fp16 AoS storage of hit
+// coordinates); every computation still runs in fp32, on the rounded values.
+struct HitsF32 {
+    using T = float4;
+    __device__ __forceinline__ static float round(float v) { return v; }
+    __device__ __forceinline__ static float4 load(const T* p, int i) { return p[i]; }
+    __device__ __forceinline__ static void store(T* p, int64_t i, float4 c) { p[i] = c; }
+};
+
+struct HitsF16 {
+    using T = ushort4;
+    __device__ __forceinline__ static float round(float v) { return __half2float(__float2half_rn(v)); }
+    __device__ __forceinline__ static float4 load(const T* p, int i)
+    {
+        const ushort4 u = p[i];
+        return make_float4(__half2float(__ushort_as_half(u.x)), __half2float(__ushort_as_half(u.y)),
+                           __half2float(__ushort_as_half(u.z)), __int_as_float((int)u.w));
+    }
+    __device__ __forceinline__ static void store(T* p, int64_t i, float4 c)
+    {
+        p[i] = make_ushort4(__half_as_ushort(__float2half_rn(c.x)), __half_as_ushort(__float2half_rn(c.y)),
+                            __half_as_ushort(__float2half_rn(c.z)), (unsigned short)__float_as_int(c.w));
+    }
+};
+
+// Sorted hits of one event, hit p as float4 (x, y, z, input index bits).
+template <class HS>
+struct HitArr {
+    const typename HS::T* p;
+    __device__ __forceinline__ float4 operator[](int i) const { return HS::load(p, i); }
+};
+
 // What one event's search sees: its sorted hits (read-only) and its scratch.
+template <class HS>
 struct Region {
-    const float4* coords;
+    HitArr<HS> coords;
     const uint16_t* phi;
     uint32_t* list;
     uint16_t* mark;
@@ -216,11 +252,12 @@ struct Region {
     int fstride;
 };
 
-__device__ inline Region region_of(const Sorted& O, int off, const Work& W, int64_t hb, int64_t r,
-                                   int cap)
+template <class HS>
+__device__ inline Region<HS> region_of(const Sorted& O, int off, const Work& W, int64_t hb, int64_t r,
+                                      int cap)
 {
-    Region R;
-    R.coords = O.coords + off;
+    Region<HS> R;
+    R.coords = HitArr<HS>{(const typename HS::T*)O.coords + off};
     R.phi = O.phi + off;
     R.list = W.list + hb;
     R.mark = W.mark + hb;
@@ -337,6 +374,7 @@ __device__ void warp_bitonic(uint32_t* a, int s)
 // phi16 << 14 | input index, a unique key, so the order is the one of a
 // stable sort by (module, phi16).  Status SBT_ERR_ARG for a module id out of
 // range, SBT_ERR_CAPACITY above the configured hit limit.
+template <class HS>
 __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, Sorted O)
 {
     constexpr int NT = kSortThreads;
@@ -384,7 +422,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
                 err = SBT_ERR_ARG;
                 m = 0;
             }
-            const uint32_t ph = phi16_of(xs[u], ys[u]);
+            const uint32_t ph = phi16_of(HS::round(xs[u]), HS::round(ys[u]));
             phi[i] = (uint16_t)ph;
             atomicAdd(&cnt[(m << 6) | (int)(ph >> 10)], 1);
         }
@@ -467,7 +505,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
             const int p = p0 + u * NT;
             if (p < n) {
                 O.phi[off + p] = (uint16_t)(en[u] >> 14);
-                O.coords[off + p] = c[u];
+                HS::store((typename HS::T*)O.coords, (int64_t)off + p, c[u]);
             }
         }
     }
@@ -522,8 +560,8 @@ __device__ __forceinline__ bool window_of(float xp, float yp, float cut, float s
 // starts at sorted index lo_idx (all hits when not windowed); the scatter of
 // every visited hit is computed exactly (rounded operations) and
 // `better(sc, b)` orders candidates under the cut.
-template <class Better, class Take>
-__device__ __forceinline__ void scan_from(const Smem& S, const Region& R, int b0, int nb, float xp,
+template <class Better, class Take, class HS>
+__device__ __forceinline__ void scan_from(const Smem& S, const Region<HS>& R, int b0, int nb, float xp,
                                           float yp, float cut, bool windowed, int lo_idx,
                                           uint32_t lo, uint32_t width, Better better, Take take)
 {
@@ -538,8 +576,8 @@ __device__ __forceinline__ void scan_from(const Smem& S, const Region& R, int b0
     }
 }
 
-template <class Better, class Take>
-__device__ __forceinline__ void scan_window(const Smem& S, const Region& R, int b0, int nb, float xp,
+template <class Better, class Take, class HS>
+__device__ __forceinline__ void scan_window(const Smem& S, const Region<HS>& R, int b0, int nb, float xp,
                                             float yp, float cut, float sqrt_cut, Better better,
                                             Take take)
 {
@@ -569,7 +607,8 @@ constexpr int kSeedBatch = 1;
 // Candidates a[0, na) of one middle hit, processed together: extrapolations,
 // then the binary searches of their windows in lockstep (independent loads in
 // flight), then the window scans.  Keeps the best (scatter, a, b).
-__device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& S, const Region& R,
+template <class HS>
+__device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& S, const Region<HS>& R,
                                                 int i0, int ni, float4 Cc, float zi, float sqrt_cut,
                                                 const int* a, int na, bool& have, float& best_sc,
                                                 int& best_a, int& best_b)
@@ -632,7 +671,8 @@ __device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& 
 // (scatter, position of a, position of b).  `outer` lists the unflagged hits
 // of module s in sorted order as (phi16 << 16 | position), `nu` of them, so
 // the nearest-first walk visits no flagged hit.
-__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int s, int c,
+template <class HS>
+__device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R, int s, int c,
                          const uint32_t* outer, int nu, float sqrt_cut, int& oa, int& ob)
 {
     const int i0 = S.modoff[s + 2], ni = S.modoff[s + 3] - i0;
@@ -683,7 +723,8 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region& R, int
 }
 
 // Following: best unflagged hit on module t for the track's last two hits.
-__device__ bool follow_best(const DevConfig& C, const Smem& S, const Region& R, int t, int h1, int h2,
+template <class HS>
+__device__ bool follow_best(const DevConfig& C, const Smem& S, const Region<HS>& R, int t, int h1, int h2,
                             float sqrt_cut, int& cand, float& csc)
 {
     const int b0 = S.modoff[t], nb = S.modoff[t + 1] - b0;
@@ -710,13 +751,15 @@ __device__ __forceinline__ unsigned long long claim_key(unsigned long long tag, 
     return tag | ((unsigned long long)__float_as_uint(score) << 16) | (unsigned long long)key;
 }
 
-__device__ __forceinline__ void add_final(const Smem& S, const Region& R, int last, int nh)
+template <class HS>
+__device__ __forceinline__ void add_final(const Smem& S, const Region<HS>& R, int last, int nh)
 {
     int k = atomicAdd(&S.misc[kNFin], 1);
     R.finals[k] = (uint32_t)last | ((uint32_t)nh << 16);
 }
 
-__device__ __forceinline__ void add_tracklet(const Smem& S, const Region& R, int h0, int h1, int h2,
+template <class HS>
+__device__ __forceinline__ void add_tracklet(const Smem& S, const Region<HS>& R, int h0, int h1, int h2,
                                              int key)
 {
     int k = atomicAdd(&S.misc[kNTl], 1);
@@ -744,7 +787,8 @@ __device__ __forceinline__ FTrack make_track(int h0, int h1, int h2, int key, in
 // Following search of one forming track to module t and its claims: the new
 // hit, and for a 3-hit track also its three hits.  A 3-hit track with a
 // flagged hit cannot extend any more and is marked dead.
-__device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem& S, const Region& R,
+template <class HS>
+__device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem& S, const Region<HS>& R,
                                                  int t, unsigned long long tag, float sqrt_cut,
                                                  FTrack& T)
 {
@@ -779,8 +823,8 @@ __device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem&
 // Claims carry a tag (64 - t) << 48 above (scatter bits, track key), so a
 // claim of an earlier step always compares larger than one of the current
 // step and the claim words need no reset between steps.
-template <int NT>
-__device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S, int n)
+template <int NT, class HS>
+__device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem& S, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const int M = C.M;
@@ -928,8 +972,8 @@ __device__ bool search_stage(const DevConfig& C, const Region& R, const Smem& S,
 
 // Tracklet filter: three unflagged hits and chi2 < C3, then one claim round
 // among the survivors (tag 0, below every search tag).
-template <int NT>
-__device__ void tracklet_filter(const DevConfig& C, const Region& R, const Smem& S)
+template <int NT, class HS>
+__device__ void tracklet_filter(const DevConfig& C, const Region<HS>& R, const Smem& S)
 {
     const int tid = threadIdx.x;
     const int ntl = min(S.misc[kNTl], R.lcap);
@@ -979,8 +1023,8 @@ __device__ void tracklet_filter(const DevConfig& C, const Region& R, const Smem&
 // track's linked hit list is walked once, into `pos` at the track's place in
 // found order; ranks then come from a running count of marks over input
 // indices, and the hit writes and fit passes read `pos` (independent loads).
-template <int NT>
-__device__ void output_stage(const DevConfig& C, int e, int off, int n, const Region& R,
+template <int NT, class HS>
+__device__ void output_stage(const DevConfig& C, int e, int off, int n, const Region<HS>& R,
                              const Smem& S, const Staging& G, const sbt_tracks& out)
 {
     const int tid = threadIdx.x;
@@ -1081,7 +1125,7 @@ __device__ __forceinline__ void fail_event(int e, int code, const Staging& G, co
 }
 
 // Search of one sorted event by the whole block.
-template <int NT>
+template <int NT, class HS>
 __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                           const Staging& G, const sbt_tracks& out, int e, int64_t hb, int64_t r,
                           int cap, const Smem& S)
@@ -1094,7 +1138,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
         fail_event(e, st != SBT_OK ? st : SBT_ERR_CAPACITY, G, out);
         return;
     }
-    Region R = region_of(O, off, W, hb, r, cap);
+    Region<HS> R = region_of<HS>(O, off, W, hb, r, cap);
     for (int m = tid; m <= C.M; m += NT) S.modoff[m] = O.modoff[(int64_t)e * (C.M + 1) + m];
     for (int w = tid; w < (n + 31) / 32; w += NT) S.flag[w] = 0u;
     for (int p = tid; p < n; p += NT) R.mark[p] = kNone;
@@ -1115,7 +1159,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
 // ------------------------------------------------------------- kernels ---
 
 // One block per event.
-template <int NT>
+template <int NT, class HS>
 __global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sorted O, Work W,
                                                       Staging G, sbt_tracks out)
 {
@@ -1124,12 +1168,12 @@ __global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sor
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
-    run_event<NT>(C, in, O, W, G, out, e, off, e, max(n, 0), S);
+    run_event<NT, HS>(C, in, O, W, G, out, e, off, e, max(n, 0), S);
 }
 
 // Persistent: each resident block takes events from the work queue in the
 // order of G.order (largest first) and reuses its own scratch region.
-template <int NT>
+template <int NT, class HS>
 __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in, Sorted O, Work W,
                                                            Staging G, sbt_tracks out)
 {
@@ -1142,7 +1186,7 @@ __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in
         const int q = S.misc[kEvent];
         __syncthreads();
         if (q >= in.n_events) break;
-        run_event<NT>(C, in, O, W, G, out, G.order[q], hb, blockIdx.x, C.nmax, S);
+        run_event<NT, HS>(C, in, O, W, G, out, G.order[q], hb, blockIdx.x, C.nmax, S);
     }
 }
 
@@ -1275,13 +1319,14 @@ __global__ void __launch_bounds__(1024) k_offset_fixup(int32_t* track_offsets, i
 }
 
 // Sort stage output copied out, for stage-level checks.
+template <class HS>
 __global__ void k_debug_sort_copy(DevConfig C, Inputs in, Sorted O, uint16_t* phi16, int32_t* perm,
                                   int32_t* modoff)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < in.n_hits) {
         phi16[i] = O.phi[i];
-        perm[i] = __float_as_int(O.coords[i].w);
+        perm[i] = __float_as_int(HS::load((const typename HS::T*)O.coords, i).w);
     }
     if (i < (int64_t)in.n_events * (C.M + 1)) modoff[i] = O.modoff[i];
 }
@@ -1297,21 +1342,22 @@ __global__ void k_debug_phi16(const float* x, const float* y, int32_t n, uint16_
 cudaError_t launch_sort(const DevConfig& C, const Inputs& in, const Sorted& O, cudaStream_t st)
 {
     size_t sm = sort_smem_bytes(C.nmax);
-    cudaError_t err = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = C.h16 ? k_sort<HitsF16> : k_sort<HitsF32>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    if (in.n_events > 0) k_sort<<<in.n_events, kSortThreads, sm, st>>>(C, in, O);
+    if (in.n_events > 0) kern<<<in.n_events, kSortThreads, sm, st>>>(C, in, O);
     return cudaGetLastError();
 }
 
-template <int NT>
+template <int NT, class HS>
 static cudaError_t plain_nt(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                             const Staging& G, const sbt_tracks& out, cudaStream_t st)
 {
     size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_search_plain<NT>,
+    cudaError_t err = cudaFuncSetAttribute(k_search_plain<NT, HS>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    if (in.n_events > 0) k_search_plain<NT><<<in.n_events, NT, sm, st>>>(C, in, O, W, G, out);
+    if (in.n_events > 0) k_search_plain<NT, HS><<<in.n_events, NT, sm, st>>>(C, in, O, W, G, out);
     return cudaGetLastError();
 }
 
@@ -1319,9 +1365,9 @@ cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Sorted& O, 
                          const Staging& S, const sbt_tracks& out, int threads, cudaStream_t stream)
 {
     switch (threads) {
-        case 64: return plain_nt<64>(C, in, O, W, S, out, stream);
-        case 128: return plain_nt<128>(C, in, O, W, S, out, stream);
-        case 256: return plain_nt<256>(C, in, O, W, S, out, stream);
+        case 64: return C.h16 ? plain_nt<64, HitsF16>(C, in, O, W, S, out, stream) : plain_nt<64, HitsF32>(C, in, O, W, S, out, stream);
+        case 128: return C.h16 ? plain_nt<128, HitsF16>(C, in, O, W, S, out, stream) : plain_nt<128, HitsF32>(C, in, O, W, S, out, stream);
+        case 256: return C.h16 ? plain_nt<256, HitsF16>(C, in, O, W, S, out, stream) : plain_nt<256, HitsF32>(C, in, O, W, S, out, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1332,15 +1378,15 @@ cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream
     return cudaGetLastError();
 }
 
-template <int NT>
+template <int NT, class HS>
 static int occupancy_nt(const DevConfig& C)
 {
     size_t sm = smem_bytes(C.nmax, NT);
-    if (cudaFuncSetAttribute(k_search_persistent<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_search_persistent<NT, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_search_persistent<NT>, NT, sm) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_search_persistent<NT, HS>, NT, sm) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -1349,23 +1395,23 @@ static int occupancy_nt(const DevConfig& C)
 int persistent_blocks_per_sm(const DevConfig& C, int threads)
 {
     switch (threads) {
-        case 64: return occupancy_nt<64>(C);
-        case 128: return occupancy_nt<128>(C);
-        case 256: return occupancy_nt<256>(C);
+        case 64: return C.h16 ? occupancy_nt<64, HitsF16>(C) : occupancy_nt<64, HitsF32>(C);
+        case 128: return C.h16 ? occupancy_nt<128, HitsF16>(C) : occupancy_nt<128, HitsF32>(C);
+        case 256: return C.h16 ? occupancy_nt<256, HitsF16>(C) : occupancy_nt<256, HitsF32>(C);
         default: return 0;
     }
 }
 
-template <int NT>
+template <int NT, class HS>
 static cudaError_t persistent_nt(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                                  const Staging& G, const sbt_tracks& out, int blocks,
                                  cudaStream_t st)
 {
     size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_search_persistent<NT>,
+    cudaError_t err = cudaFuncSetAttribute(k_search_persistent<NT, HS>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    if (blocks > 0) k_search_persistent<NT><<<blocks, NT, sm, st>>>(C, in, O, W, G, out);
+    if (blocks > 0) k_search_persistent<NT, HS><<<blocks, NT, sm, st>>>(C, in, O, W, G, out);
     return cudaGetLastError();
 }
 
@@ -1374,9 +1420,9 @@ cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Sorted
                               cudaStream_t stream)
 {
     switch (threads) {
-        case 64: return persistent_nt<64>(C, in, O, W, S, out, blocks, stream);
-        case 128: return persistent_nt<128>(C, in, O, W, S, out, blocks, stream);
-        case 256: return persistent_nt<256>(C, in, O, W, S, out, blocks, stream);
+        case 64: return C.h16 ? persistent_nt<64, HitsF16>(C, in, O, W, S, out, blocks, stream) : persistent_nt<64, HitsF32>(C, in, O, W, S, out, blocks, stream);
+        case 128: return C.h16 ? persistent_nt<128, HitsF16>(C, in, O, W, S, out, blocks, stream) : persistent_nt<128, HitsF32>(C, in, O, W, S, out, blocks, stream);
+        case 256: return C.h16 ? persistent_nt<256, HitsF16>(C, in, O, W, S, out, blocks, stream) : persistent_nt<256, HitsF32>(C, in, O, W, S, out, blocks, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1412,8 +1458,9 @@ cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const S
 {
     const int64_t n = std::max<int64_t>(in.n_hits, (int64_t)in.n_events * (C.M + 1));
     if (n > 0)
-        k_debug_sort_copy<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(C, in, O, phi16, perm,
-                                                                           module_offsets);
+        (C.h16 ? k_debug_sort_copy<HitsF16> : k_debug_sort_copy<HitsF32>)<<<(unsigned)((n + 255) / 256), 256, 0,
+                                                                          stream>>>(C, in, O, phi16, perm,
+                                                                                    module_offsets);
     return cudaGetLastError();
 }
 

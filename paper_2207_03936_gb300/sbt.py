@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("max_scatter_follow", ctypes.c_float), ("max_chi2_tracklet", ctypes.c_float),
                 ("hit_sigma", ctypes.c_float), ("max_hits_per_event", ctypes.c_int32),
                 ("max_forming_tracks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("gec_max_hits", ctypes.c_int32)]
+                ("gec_max_hits", ctypes.c_int32), ("fp16_hits", ctypes.c_int32)]
 
 
 class TracksC(ctypes.Structure):

@@ -194,6 +194,31 @@ def test_global_event_cut(sbt, batched):
     assert np.array_equal(g["chi2"].view(np.uint32), want["chi2"].view(np.uint32))
 
 
+@pytest.mark.parametrize("config,n", [(2, 300), (3, 150)])
+def test_fp16_hit_storage_bit_exact(sbt, config, n):
+    """fp16 hit storage: plain and batched equal the oracle run on coordinates
+    rounded to fp16; the sort stage equals the oracle's sort of them."""
+    ev = synth.make_events(config, n)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(fp16_hits=1, **CFG))
+    try:
+        o = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                               oracle.config(**CFG), fp16_hits=True)
+        assert_same(run_gpu(sbt, h, ev, False), o)
+        assert_same(run_gpu(sbt, h, ev, True), o)
+        phi, perm, mo = sbt.sbt_debug_sort(h, *[to_dev(ev)[i] for i in (0, 1, 3, 4)])
+        torch.cuda.synchronize()
+    finally:
+        h.close()
+    phi = phi.cpu().numpy().view(np.uint16)
+    perm = perm.cpu().numpy()
+    xr, yr = oracle.round_fp16(ev.x), oracle.round_fp16(ev.y)
+    for e in range(0, ev.n_events, 7):
+        lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+        p, _, ph = oracle.sort_event(xr[lo:hi], yr[lo:hi], ev.module[lo:hi], 52)
+        assert np.array_equal(perm[lo:hi], p)
+        assert np.array_equal(phi[lo:hi], ph)
+
+
 def test_uneven_workload_bit_exact(sbt, handle):
     ev = synth.make_events(3, 400)
     o = oracle_of(ev)
