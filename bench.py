@@ -147,12 +147,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def serve(sbt, h, ev, rate_hz, budget_bytes, streams=8, max_batch=512, timeout=120.0):
-    """Open-loop Poisson arrivals at rate_hz into the request loop; returns
-    events/s (completions over the span from first arrival to last
+def serve(sbt, srv, ev, rate_hz, budget_bytes, timeout=120.0):
+    """Open-loop Poisson arrivals at rate_hz into a running request loop;
+    returns events/s (completions over the span from first arrival to last
     completion) and submit-to-done latency percentiles."""
-    srv = sbt.Server(h, budget_bytes, streams, max_batch)
-    try:
+    st0 = srv.stats()
+    if True:
         if rate_hz is None:
             arrival = np.zeros(ev.n_events)
         else:
@@ -168,13 +168,14 @@ def serve(sbt, h, ev, rate_hz, budget_bytes, streams=8, max_batch=512, timeout=1
         span = time.perf_counter() - t0
         lat = np.concatenate(lat) if lat else np.zeros(0)
         st = srv.stats()
-    finally:
-        srv.close()
+    nb = st["batches"] - st0["batches"]
+    mean_batch = ((st["mean_batch_events"] * st["batches"] - st0["mean_batch_events"] * st0["batches"]) / nb
+                  if nb > 0 else 0.0)
     return {"offered_hz": rate_hz, "events": int(len(lat)), "value": len(lat) / span,
             "unit": "events/s", "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
-            "budget_gb": budget_bytes / 2**30, "mean_batch_events": st["mean_batch_events"],
-            "peak_inflight_gb": st["peak_bytes"] / 2**30}
+            "budget_gb": budget_bytes / 2**30, "mean_batch_events": mean_batch,
+            "peak_inflight_gb_server_lifetime": st["peak_bytes"] / 2**30}
 
 
 def cpu_baseline(ev, budget_s: float, gpu_out=None):
@@ -455,11 +456,25 @@ def main():
                "events": ev_adj.n_events, "tracks": int(rc["counts"][0]), "dtype": "f64"}
     serving = None
     if ev_srv is not None:
-        sat = serve(sbt, h, ev_srv, None, 4 << 30)          # all events at once: saturation
+        # one long-lived server per memory budget (8 stream slots, batches of at
+        # most 512 events), warmed up by one schedule before anything is timed
         rates = [0.5, 0.9] if not args.serving_sweep else [0.1, 0.3, 0.5, 0.7, 0.9, 1.1, 1.3, 1.5]
         budgets = [4 << 30] if not args.serving_sweep else [2 << 30, 4 << 30, 8 << 30, 16 << 30]
-        runs = [serve(sbt, h, ev_srv, f * sat["value"], b) for b in budgets for f in rates]
+        servers = {}
+
+        def server(b):
+            if b not in servers:
+                servers[b] = sbt.Server(h, b, 8, 512)
+                serve(sbt, servers[b], ev_srv, None, b)  # warm-up: buffers and pools reach size
+            return servers[b]
+        try:
+            sat = serve(sbt, server(4 << 30), ev_srv, None, 4 << 30)   # all events at once
+            runs = [serve(sbt, server(b), ev_srv, f * sat["value"], b) for b in budgets for f in rates]
+        finally:
+            for v in servers.values():
+                v.close()
         serving = {"workload": "upgrade-condition events, open-loop Poisson arrivals",
+                   "server": "long-lived, warmed up by one schedule of the same events",
                    "saturation": sat, "runs": runs,
                    "p99_ms_at_0.9x": next((r["p99_ms"] for r in runs
                                           if abs(r["offered_hz"] - 0.9 * sat["value"]) < 1e-6), None)}

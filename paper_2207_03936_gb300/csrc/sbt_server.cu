@@ -413,6 +413,8 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
     cfg.max_hits_per_event = C.nmax;
     cfg.max_forming_tracks = C.fcap;
     cfg.threads_per_block = sbt::handle_plain_threads(h);
+    cfg.gec_max_hits = C.gec;
+    cfg.fp16_hits = C.h16;
     for (int i = 0; i < max_streams && e == cudaSuccess; i++) {
         auto sl = std::make_unique<Slot>();
         if (sbt_create(&g, &cfg, &sl->h) != SBT_OK) {
