@@ -375,7 +375,8 @@ def main():
         hk = sbt.sbt_profile_batched(hh, *dev, hout, reps=2)
         fp16 = {"value": ev.n_events / (hms / 1e3), "unit": "events/s", "ms_per_step": hms,
                 "speedup": ms / hms, "tracks": int(hout.counts[0].item()), "tracks_fp32": T,
-                "kernel_ms": {"sort": hk[1], "search": hk[2]}}
+                "kernel_ms": {"sort": hk[1], "search": hk[2]},
+                "search_traffic": profiled_traffic("k_search_persistent_fp16", ev.n_hits)}
         hh.close()
         del hout
 
