@@ -309,7 +309,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 
 // ------------------------------------------------------------- sorting ---
 
-constexpr int kSortThreads = 512;
+constexpr int kSortThreads = 1024;
 constexpr int kSortBuckets = 4096;  // (module, top six bits of phi16)
 constexpr int kShortBucket = 32;    // buckets up to this size are sorted by one thread
 
@@ -375,7 +375,7 @@ __device__ void warp_bitonic(uint32_t* a, int s)
 // stable sort by (module, phi16).  Status SBT_ERR_ARG for a module id out of
 // range, SBT_ERR_CAPACITY above the configured hit limit.
 template <class HS>
-__global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, Sorted O)
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort(DevConfig C, Inputs in, Sorted O)
 {
     constexpr int NT = kSortThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -401,12 +401,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
         nlong = 0;
     }
     __syncthreads();
-    // phi16 and bucket counts, four hits per thread per round (loads first)
-    for (int i0 = tid; i0 < n; i0 += 4 * NT) {
-        float xs[4], ys[4];
-        int ms[4];
+    // phi16 and bucket counts, two hits per thread per round (loads first)
+    for (int i0 = tid; i0 < n; i0 += 2 * NT) {
+        float xs[2], ys[2];
+        int ms[2];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 2; u++) {
             const int i = i0 + u * NT;
             const bool v = i < n;
             xs[u] = v ? in.x[off + i] : 1.0f;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
             ms[u] = v ? in.module[off + i] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 2; u++) {
             const int i = i0 + u * NT;
             if (i >= n) continue;
             int m = ms[u];
@@ -487,12 +487,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
     for (int m = tid; m <= C.M; m += NT)
         O.modoff[(int64_t)e * (C.M + 1) + m] = m == 0 ? 0 : (m < C.M ? cnt[(m << 6) - 1] : n);
     __syncthreads();
-    // gather of the sorted hits, four per thread per round
-    for (int p0 = tid; p0 < n; p0 += 4 * NT) {
-        float4 c[4];
-        uint32_t en[4];
+    // gather of the sorted hits, two per thread per round
+    for (int p0 = tid; p0 < n; p0 += 2 * NT) {
+        float4 c[2];
+        uint32_t en[2];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 2; u++) {
             const int p = p0 + u * NT;
             if (p < n) {
                 en[u] = ent[p];
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(DevConfig C, Inputs in, S
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 2; u++) {
             const int p = p0 + u * NT;
             if (p < n) {
                 O.phi[off + p] = (uint16_t)(en[u] >> 14);
