@@ -76,3 +76,34 @@ def test_overlapping_admission_and_failure_recovery():
         lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
         one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], ev.module_z)
         assert np.array_equal(r.track_hits, one.track_hits)
+
+
+def test_served_results_keep_storage_and_event_cut_settings():
+    """Server slots reconstruct with the settings of the handle they are
+    created from: fp16 hit storage and the global event cut."""
+    from paper_2207_03936_gb300 import sbt
+    ev = synth.make_events(2, 120, workers=1)
+    sizes = np.diff(ev.event_offsets)
+    thr = int(np.quantile(sizes, 0.8))
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(fp16_hits=1, gec_max_hits=thr))
+    srv = sbt.Server(h, memory_budget_bytes=64 << 20, max_streams=2, max_batch_events=16)
+    try:
+        srv.submit_schedule(ev, np.zeros(ev.n_events))
+        got = collect(srv, ev.n_events)
+    finally:
+        srv.close()
+        h.close()
+    assert len(got) == ev.n_events
+    cfg = oracle.config()
+    for e in range(ev.n_events):
+        r = got[e]
+        if sizes[e] > thr:
+            assert r.status == sbt.SBT_EVENT_CUT and len(r.hit_offsets) == 1
+            continue
+        lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+        one = oracle.event(oracle.round_fp16(ev.x[lo:hi]), oracle.round_fp16(ev.y[lo:hi]),
+                           oracle.round_fp16(ev.z[lo:hi]), ev.module[lo:hi], ev.module_z, cfg)
+        assert r.status == 0
+        assert np.array_equal(r.hit_offsets, one.hit_offsets)
+        assert np.array_equal(r.track_hits, one.track_hits)
+        assert np.array_equal(r.params.view(np.uint32), one.params.view(np.uint32))
