@@ -139,7 +139,8 @@ sbt_status sbt_reconstruct(sbt_handle* h, const float* x, const float* y, const 
 
 /*
  * Same result as sbt_reconstruct, produced by one persistent launch whose
- * blocks take events (largest first) from a device work queue; the launch
+ * blocks take events from a device work queue (sizes alternating between the
+ * largest and the smallest events not yet taken); the launch
  * sequence is captured once into a CUDA graph per distinct argument set and
  * replayed.  Block size comes from sbt_autotune when it has run.
  */

@@ -1171,8 +1171,9 @@ __global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sor
     run_event<NT, HS>(C, in, O, W, G, out, e, off, e, max(n, 0), S);
 }
 
-// Persistent: each resident block takes events from the work queue in the
-// order of G.order (largest first) and reuses its own scratch region.
+// Persistent: each resident block takes events from the work queue, sizes
+// alternating from both ends of G.order (largest first), and reuses its own
+// scratch region.
 template <int NT, class HS>
 __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in, Sorted O, Work W,
                                                            Staging G, sbt_tracks out)
@@ -1186,7 +1187,12 @@ __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in
         const int q = S.misc[kEvent];
         __syncthreads();
         if (q >= in.n_events) break;
-        run_event<NT, HS>(C, in, O, W, G, out, G.order[q], hb, blockIdx.x, C.nmax, S);
+        // alternately the largest and the smallest event not yet taken: the
+        // resident events' hits and scratch stay near the average size (the
+        // largest-first order alone fills L2 with the heaviest events at the
+        // start), and the last events taken are mid-sized
+        const int qi = (q & 1) ? in.n_events - 1 - (q >> 1) : (q >> 1);
+        run_event<NT, HS>(C, in, O, W, G, out, G.order[qi], hb, blockIdx.x, C.nmax, S);
     }
 }
 
