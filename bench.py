@@ -323,6 +323,23 @@ def main():
     sort_bytes = 16 * ev.n_hits + 4 * (ev.n_events + 1) + 18 * ev.n_hits + 4 * 54 * ev.n_events
     sort_gbs = sort_bytes / (kms[1] / 1e3) / 1e9
 
+    # end to end through the host entry point (pinned host buffers)
+    host_in = [torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+    hout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, pin_memory=True)
+    sbt.sbt_reconstruct_host(h, *host_in, out=hout)
+    n_e2e = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sbt.sbt_reconstruct_host(h, *host_in, out=hout)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_ms_max, e2e_value = job_throughput(e2e_s * 1e3, ev.n_events, ws, pg, "cuda")
+    h2d = 16 * ev.n_hits + 4 * (ev.n_events + 1)
+    d2h = 16 + 4 * (ev.n_events + 1) + 4 * ev.n_events + 4 * (T + 1) + 4 * H + 24 * T
+    e2e = {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max}
+    del hout, host_in
+
     plain = None
     if not args.no_plain:
         pout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
@@ -363,6 +380,7 @@ def main():
                      "tracks": int(aout.counts[0].item()), "tracks_descending": T}
         ha.close()
         del aout, dev_asc
+        torch.cuda.empty_cache()
 
     # fp16 hit storage (x, y, z rounded to fp16, 8 bytes per sorted hit)
     fp16 = None
@@ -387,6 +405,7 @@ def main():
                 "search_traffic": profiled_traffic("k_search_persistent_fp16", ev.n_hits)}
         hh.close()
         del hout
+        torch.cuda.empty_cache()
 
     # global event cut: the busiest 10% of events rejected unreconstructed;
     # throughput over all input events, physics traded on a truth sample
@@ -428,23 +447,7 @@ def main():
                           "clone_fraction_with_cut": cut_ind["clone_fraction"]}}
         hg.close()
         del gout, gres
-
-    # end to end through the host entry point (pinned host buffers)
-    host_in = [torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
-    hout = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, pin_memory=True)
-    sbt.sbt_reconstruct_host(h, *host_in, out=hout)
-    n_e2e = max(1, min(args.steps, 3))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        sbt.sbt_reconstruct_host(h, *host_in, out=hout)
-    e2e_s = (time.perf_counter() - t0) / n_e2e
-    e2e_ms_max, e2e_value = job_throughput(e2e_s * 1e3, ev.n_events, ws, pg, "cuda")
-    h2d = 16 * ev.n_hits + 4 * (ev.n_events + 1)
-    d2h = 16 + 4 * (ev.n_events + 1) + 4 * ev.n_events + 4 * (T + 1) + 4 * H + 24 * T
-    e2e = {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max}
-    del hout, host_in
+        torch.cuda.empty_cache()
 
     adj = None
     if ev_adj is not None:

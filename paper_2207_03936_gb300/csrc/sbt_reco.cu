@@ -1301,7 +1301,16 @@ __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Sta
     }
     const int32_t* src = G.hits + off;
     int32_t* dst = out.track_hits + hbse;
-    for (int j = lane; j < H; j += 32) dst[j] = src[j];
+    // four independent loads in flight per lane
+    int j = lane;
+    for (; j + 96 < H; j += 128) {
+        const int32_t a = src[j], b = src[j + 32], c = src[j + 64], d = src[j + 96];
+        dst[j] = a;
+        dst[j + 32] = b;
+        dst[j + 64] = c;
+        dst[j + 96] = d;
+    }
+    for (; j < H; j += 32) dst[j] = src[j];
 }
 
 // Chunked host pipeline: adds the totals of the earlier chunks to one chunk's
