@@ -1187,11 +1187,13 @@ __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in
         const int q = S.misc[kEvent];
         __syncthreads();
         if (q >= in.n_events) break;
-        // alternately the largest and the smallest event not yet taken: the
-        // resident events' hits and scratch stay near the average size (the
-        // largest-first order alone fills L2 with the heaviest events at the
-        // start), and the last events taken are mid-sized
-        const int qi = (q & 1) ? in.n_events - 1 - (q >> 1) : (q >> 1);
+        // alternately the largest and the smallest event not yet taken, so
+        // the resident events' hits and scratch stay near the average size
+        // (the largest-first order alone fills L2 with the heaviest events at
+        // the start); the last 2 x blocks events, from the middle of the size
+        // order, are taken largest first, which keeps the tail short
+        const int q0 = max(0, in.n_events - 2 * (int)gridDim.x) & ~1;
+        const int qi = q >= q0 ? (q0 >> 1) + (q - q0) : (q & 1) ? in.n_events - 1 - (q >> 1) : (q >> 1);
         run_event<NT, HS>(C, in, O, W, G, out, G.order[qi], hb, blockIdx.x, C.nmax, S);
     }
 }
