@@ -501,7 +501,7 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
         *dndof = cv.take<int32_t>(H / 3 + 2 * C);
         *dstat = cv.take<int32_t>(E);
         *dcnt = cv.take<int32_t>(4 * C);
-        *drun = cv.take<int64_t>(2);
+        *drun = cv.take<int64_t>(2 * (C + 1));
     };
     float *dx, *dy, *dz, *dpar, *dchi;
     int32_t *dm, *doff, *dto, *dho, *dth, *dndof, *dstat, *dcnt;
@@ -544,7 +544,7 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
         }
         if (e == cudaSuccess) e = cudaEventRecord(in_ev[c], h->copy_in);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(drun, 0, 2 * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(drun, 0, 2 * sizeof(int64_t), s);  // totals before chunk 0
     // per-chunk reconstruction; chunk c's outputs start at event e0[c] + c,
     // track slot hits/3 + 2c and hit slot hits + c of the device buffers
     std::vector<sbt_tracks> dc(C);
@@ -572,7 +572,8 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
                 return st;
             }
         }
-        if (e == cudaSuccess) e = launch_offset_fixup(d.track_offsets, Ec, d.hit_offsets, d.counts, drun, s);
+        if (e == cudaSuccess)
+            e = launch_offset_fixup(d.track_offsets, Ec, d.hit_offsets, d.counts, drun + 2 * c, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h->host_counts + 4 * c, d.counts, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(comp_ev[c], s);

@@ -117,6 +117,10 @@ cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const S
                                    cudaStream_t stream);
 cudaError_t launch_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* out,
                                cudaStream_t stream);
+// Adds running[0] to track_offsets[0..n_events] and running[1] to
+// hit_offsets[0..counts[0]] (when counts[2] is SBT_OK), and writes the new
+// totals to running[2..3].
+constexpr int kFixupBlocks = 304;
 cudaError_t launch_offset_fixup(int32_t* track_offsets, int32_t n_events, int32_t* hit_offsets,
                                 const int32_t* counts, int64_t* running, cudaStream_t stream);
 int persistent_blocks_per_sm(const DevConfig& C, int threads);

@@ -1318,20 +1318,25 @@ __global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Sta
 // Chunked host pipeline: adds the totals of the earlier chunks to one chunk's
 // CSR offsets (track_offsets [n_events + 1], hit_offsets [counts[0] + 1]) and
 // advances the running totals (running[0] tracks, running[1] hits).
-__global__ void __launch_bounds__(1024) k_offset_fixup(int32_t* track_offsets, int32_t n_events,
-                                                       int32_t* hit_offsets, const int32_t* counts,
-                                                       int64_t* running)
+// Chunk offsets made global: running[0..1] hold the tracks and track hits of
+// the earlier chunks (read by every block), running[2..3] receive the totals
+// including this chunk (written by block 0 only).
+__global__ void __launch_bounds__(256) k_offset_fixup(int32_t* track_offsets, int32_t n_events,
+                                                      int32_t* hit_offsets, const int32_t* counts,
+                                                      int64_t* running)
 {
     const int64_t bt = running[0], bh = running[1];
     const int T = counts[0];
     const bool ok = counts[2] == SBT_OK;
-    for (int i = threadIdx.x; i <= n_events; i += 1024) track_offsets[i] += (int32_t)bt;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_events; i += stride)
+        track_offsets[i] += (int32_t)bt;
     if (ok)
-        for (int t = threadIdx.x; t <= T; t += 1024) hit_offsets[t] += (int32_t)bh;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        running[0] = bt + T;
-        running[1] = bh + counts[1];
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= T; t += stride)
+            hit_offsets[t] += (int32_t)bh;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        running[2] = bt + T;
+        running[3] = bh + counts[1];
     }
 }
 
@@ -1484,7 +1489,7 @@ cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const S
 cudaError_t launch_offset_fixup(int32_t* track_offsets, int32_t n_events, int32_t* hit_offsets,
                                 const int32_t* counts, int64_t* running, cudaStream_t stream)
 {
-    k_offset_fixup<<<1, 1024, 0, stream>>>(track_offsets, n_events, hit_offsets, counts, running);
+    k_offset_fixup<<<kFixupBlocks, 256, 0, stream>>>(track_offsets, n_events, hit_offsets, counts, running);
     return cudaGetLastError();
 }
 
