@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--events", type=int, default=100_000)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--threads", type=int, default=0, choices=[0, 64, 128, 256],
+                   help="search block size; 0 = autotuned on the batch")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-serving", action="store_true")
@@ -283,7 +285,13 @@ def main():
     # per-event capacity sized to the batch (shared memory per block scales with it)
     nmax = int(-(-int(np.diff(ev.event_offsets).max()) // 1024) * 1024)
     h = sbt.sbt_create(ev.module_z, sbt.default_config(max_hits_per_event=nmax))
-    threads = sbt.sbt_autotune(h, *dev)
+    if args.threads:
+        h.close()
+        h = sbt.sbt_create(ev.module_z, sbt.default_config(max_hits_per_event=nmax,
+                                                           threads_per_block=args.threads))
+        threads = args.threads
+    else:
+        threads = sbt.sbt_autotune(h, *dev)
     out = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -515,7 +523,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": profiled_traffic("k_search_persistent", ev.n_hits),
-                         "traffic_source": "ncu capture of 4000 events scaled per hit",
+                         "traffic_source": "single-pass ncu capture of the full-size launch (profiles/traffic.json)",
                          "peak_kind": peak_kind,
                          "kernel": "k_search_persistent", "kernel_ms": kms[2],
                          "kernel_ms_all": {"order": kms[0], "sort": kms[1], "search": kms[2],
