@@ -224,7 +224,7 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
  * application that owns the device memory pool.  The paper has no
  * counterpart; it computes exactly what sbt_reconstruct computes.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *     workspace is a fixed array of about 39 MB inside the library's device
+ *     workspace is a fixed array of about 40 MB inside the library's device
  *     image, held by every GPU that loads the library until the process exits.
  *   - At most 524288 hits and 4096 events per call; larger batches return
  *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).
