@@ -70,18 +70,28 @@ def dist_env():
     return ws, rank, local
 
 
+def code_digest(path):
+    """sha256 of a C/CUDA source with its comments and whitespace removed:
+    changes to the code change it, changes to the comments do not."""
+    import re
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
+
+
 def profiled_traffic(kernel, hits):
     """DRAM bytes of one launch of `kernel` over `hits` hits, scaled from the
-    committed ncu capture (bytes per hit); None once the kernel source differs
+    committed ncu capture (bytes per hit); None once the kernel code differs
     from the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    with open(os.path.join(ROOT, d["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != d["source_sha256"]:
-            return None
+    if code_digest(os.path.join(ROOT, d["source"])) != d["source_code_sha256"]:
+        return None
     k = d["kernels"].get(kernel)
     if k is None:
         return None

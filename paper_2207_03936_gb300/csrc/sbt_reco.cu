@@ -2,9 +2,11 @@
 //
 // Events map to thread blocks, hits and forming tracks to threads (Table 1
 // of the paper).  Two kernels per event:
-//   1. k_sort: phi16 of every hit and a stable LSD radix sort of (module,
-//      phi16) in three passes in shared memory (section "Sort by phi"); the
-//      sorted hits are written as AoS float4 (x, y, z, input index) + phi16;
+//   1. k_sort: phi16 of every hit and its order by (module, phi16, input
+//      index) from one counting pass into (module, coarse phi) buckets and a
+//      sort inside each bucket, in shared memory (section "Sort by phi"); the
+//      sorted hits are written as AoS records (x, y, z, input index: float4,
+//      or fp16 x, y, z and a 16-bit index) + phi16;
 //   2. k_search_*: for every module triplet (s, s+1, s+2): seeding over the unflagged
 //      middle hits, then following of every forming track to module s+3 with
 //      one-round claims on the hits, flags, and termination after two misses
@@ -14,7 +16,7 @@
 //      ordering of the tracks by smallest input hit index, staging of their
 //      hit lists and the least-squares fit of every track.
 // A device-wide scan and a consolidation kernel then build the CSR output
-// and fit every track (section "Results", data consolidation).
+// from the staged hit lists and fits (section "Results", data consolidation).
 //
 // Decision arithmetic is fp32 with every operation rounded as written
 // (explicit _rn intrinsics, no contraction), so that the result is the
