@@ -120,7 +120,7 @@ size_t carve_staging(void* base, int64_t n_hits, int64_t n_events, Staging* S)
     s.track_base = c.take<int32_t>(n_events);
     s.hit_base = c.take<int32_t>(n_events);
     s.order = c.take<int32_t>(n_events);
-    s.queue = c.take<int32_t>(4);
+    s.queue = c.take<int32_t>(4 * kMaxChunks);  // one work-queue head per host-pipeline chunk
     if (S) *S = s;
     return c.off + 256;
 }
@@ -145,7 +145,7 @@ struct sbt_handle {
     Arena plain_arena, pers_arena, stage_arena, host_arena, misc_arena, sorted_arena;
     int tuned_threads = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, sort_stream = nullptr;
     int32_t* host_counts = nullptr;  // pinned, 4 per chunk of the host pipeline
     cudaGraphExec_t exec = nullptr;
     GraphKey key{};
@@ -352,6 +352,7 @@ sbt_status sbt_destroy(sbt_handle* h)
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->copy_in) cudaStreamDestroy(h->copy_in);
     if (h->copy_out) cudaStreamDestroy(h->copy_out);
+    if (h->sort_stream) cudaStreamDestroy(h->sort_stream);
     if (h->host_counts) cudaFreeHost(h->host_counts);
     h->plain_arena.release();
     h->sorted_arena.release();
@@ -469,6 +470,7 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     cudaError_t e = cudaSuccess;
     if (!h->copy_in) e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
     if (e == cudaSuccess && !h->copy_out) e = cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->sort_stream) e = cudaStreamCreateWithFlags(&h->sort_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !h->host_counts) e = cudaMallocHost(&h->host_counts, sizeof(int32_t) * 4 * kMaxChunks);
     if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline set-up");
     // chunks of whole events: inputs of chunk c+1 upload while chunk c
@@ -520,14 +522,16 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     if ((st = ensure_staging(h, n_hits, n_events, &S)) != SBT_OK) return st;
     if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) return st;
     if ((st = ensure_sorted(h, n_hits, n_events, &O)) != SBT_OK) return st;
-    std::vector<cudaEvent_t> in_ev(C), comp_ev(C);
+    std::vector<cudaEvent_t> in_ev(C), sort_ev(C), comp_ev(C);
     for (int c = 0; c < C; c++) {
         cudaEventCreateWithFlags(&in_ev[c], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&sort_ev[c], cudaEventDisableTiming);
         cudaEventCreateWithFlags(&comp_ev[c], cudaEventDisableTiming);
     }
     auto cleanup = [&]() {
         for (int c = 0; c < C; c++) {
             cudaEventDestroy(in_ev[c]);
+            cudaEventDestroy(sort_ev[c]);
             cudaEventDestroy(comp_ev[c]);
         }
     };
@@ -546,8 +550,29 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(drun, 0, 2 * sizeof(int64_t), s);  // totals before chunk 0
     // per-chunk reconstruction; chunk c's outputs start at event e0[c] + c,
-    // track slot hits/3 + 2c and hit slot hits + c of the device buffers
+    // track slot hits/3 + 2c and hit slot hits + c of the device buffers.
+    // Every chunk has its own slice of the per-event sorted and staged arrays
+    // (the hit-indexed ones are disjoint already), so a chunk's order and
+    // sort run on the sort stream as soon as its inputs are up, in the tail
+    // of the previous chunk's search; the searches, which share the
+    // persistent scratch, stay in order on the compute stream.
     std::vector<sbt_tracks> dc(C);
+    auto chunk_views = [&](int c, Sorted& Oc, Staging& Sc) {
+        const int64_t ev0 = e0[c];
+        Oc = O;
+        Oc.modoff = O.modoff + ev0 * (h->C.M + 1);
+        Oc.status = O.status + ev0;
+        Sc = S;
+        Sc.len = S.len + ev0;  // slot off/3 + event: the chunk-local event index plus e0[c]
+        Sc.fit = S.fit + ev0;
+        Sc.chi2 = S.chi2 + ev0;
+        Sc.ev_ntracks = S.ev_ntracks + ev0;
+        Sc.ev_nhits = S.ev_nhits + ev0;
+        Sc.track_base = S.track_base + ev0;
+        Sc.hit_base = S.hit_base + ev0;
+        Sc.order = S.order + ev0;
+        Sc.queue = S.queue + 4 * c;
+    };
     for (int c = 0; c < C && e == cudaSuccess; c++) {
         const int32_t Ec = e0[c + 1] - e0[c];
         const int64_t a = event_offsets[e0[c]], b = event_offsets[e0[c + 1]];
@@ -563,15 +588,19 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
         d.counts = dcnt + 4 * c;
         d.cap_tracks = (int32_t)((b - a) / 3 + 1);
         d.cap_hits = (int32_t)(b - a + 1);
-        e = cudaStreamWaitEvent(s, in_ev[c], 0);
         Inputs in = make_inputs(dx, dy, dz, dm, doff + e0[c], Ec, (int32_t)b);
-        if (e == cudaSuccess) {
-            st = enqueue_batched(h, in, O, S, W, d, threads, blocks, s);
-            if (st != SBT_OK) {
-                cleanup();
-                return st;
-            }
-        }
+        Sorted Oc;
+        Staging Sc;
+        chunk_views(c, Oc, Sc);
+        cudaStream_t so = h->sort_stream;
+        e = cudaStreamWaitEvent(so, in_ev[c], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(Sc.queue, 0, 4 * sizeof(int32_t), so);
+        if (e == cudaSuccess && Ec > 0) e = launch_order(in, Sc, so);
+        if (e == cudaSuccess && Ec > 0) e = launch_sort(h->C, in, Oc, so);
+        if (e == cudaSuccess) e = cudaEventRecord(sort_ev[c], so);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, sort_ev[c], 0);
+        if (e == cudaSuccess && Ec > 0) e = launch_persistent(h->C, in, Oc, W, Sc, d, threads, std::min(blocks, Ec), s);
+        if (e == cudaSuccess) e = launch_finish(h->C, in, Sc, d, s);
         if (e == cudaSuccess)
             e = launch_offset_fixup(d.track_offsets, Ec, d.hit_offsets, d.counts, drun + 2 * c, s);
         if (e == cudaSuccess)
