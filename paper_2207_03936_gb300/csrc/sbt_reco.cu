@@ -152,7 +152,7 @@ __device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* par
 
 enum Misc {
     kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kNOuter = 7,
-    kNew = 8, kMiscN = 32
+    kNew = 8, kWork = 9, kMiscN = 32
 };
 
 // Per-block shared memory of the search: flag bits, module offsets, counters.
@@ -819,8 +819,10 @@ __device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem&
 // Iterative seeding and following.  Returns false (uniformly) on overflow.
 // Per module triplet (s, s+1, s+2) three phases separated by barriers:
 //   P0  work lists: unflagged middle hits of s+1, unflagged hits of s in order;
-//   P1  following of the forming tracks to t = s+3 with claims, and seeding
-//       (every new seed searches its own continuation at once);
+//   P1  seeding and following of the forming tracks to t = s+3 with claims
+//       (every new seed searches its own continuation at once); threads take
+//       work items from a shared counter, seeds (the costlier items) first,
+//       so the step's barrier waits on a balanced tail;
 //   P2  resolution of the claims, flags, termination.
 // Claims carry a tag (64 - t) << 48 above (scatter bits, track key), so a
 // claim of an earlier step always compares larger than one of the current
@@ -853,6 +855,7 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
         if (tid == 0) {
             misc[kCnt0 + nxt] = 0;
             misc[kNew] = 0;
+            misc[kWork] = 0;
         }
         if (s + 3 <= M - 1)  // claim words of the target module start empty
             for (int p = S.modoff[s + 3] + tid; p < S.modoff[s + 4]; p += NT) R.claim[p] = ~0ull;
@@ -889,15 +892,17 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
         const bool follow = t <= M - 1;
         const unsigned long long tag = (unsigned long long)(64 - t) << 48;
         // P1
-        for (int i = tid; i < nold + nl; i += NT) {
-            if (i < nold) {
+        for (;;) {
+            const int i = atomicAdd(&misc[kWork], 1);
+            if (i >= nold + nl) break;
+            if (i >= nl) {
                 if (follow) {
-                    FTrack T = Fc[i];
+                    FTrack T = Fc[i - nl];
                     follow_and_claim(C, S, R, t, tag, sq_follow, T);
-                    Fc[i] = T;
+                    Fc[i - nl] = T;
                 }
             } else {
-                const int c = (int)list[i - nold];
+                const int c = (int)list[i];
                 int a, b;
                 if (seed_for(C, S, R, s, c, outer, nu, sq_seed, a, b)) {
                     const int slot = nold + atomicAdd(&misc[kNew], 1);
