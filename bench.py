@@ -81,10 +81,12 @@ def code_digest(path):
     return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
 
 
-def profiled_traffic(kernel, hits):
-    """DRAM bytes of one launch of `kernel` over `hits` hits, scaled from the
-    committed ncu capture (bytes per hit); None once the kernel code differs
-    from the one the counters were taken on."""
+def profiled(kernel, hits):
+    """Counters of one launch of `kernel` (name<threads>) from the committed
+    single-pass ncu capture of the full-size workload: DRAM bytes read and
+    written, warp instructions and thread instructions issued.  None when the
+    batch is not the captured one (per-hit figures depend on the batch size)
+    or the kernel code differs from the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -93,9 +95,31 @@ def profiled_traffic(kernel, hits):
     if code_digest(os.path.join(ROOT, d["source"])) != d["source_code_sha256"]:
         return None
     k = d["kernels"].get(kernel)
-    if k is None:
+    if k is None or k["hits"] != hits:
         return None
-    return (k["dram_read_bytes"] + k["dram_write_bytes"]) / k["hits"] * hits
+    return k
+
+
+def profiled_traffic(kernel, hits):
+    """DRAM bytes of one launch of `kernel` (dram__bytes_read.sum +
+    dram__bytes_write.sum of the committed capture), or None."""
+    k = profiled(kernel, hits)
+    return None if k is None else k["dram_read_bytes"] + k["dram_write_bytes"]
+
+
+def issue_roofline(kernel, hits, kernel_ms, sm_mhz, sm_count):
+    """Warp-instruction issue rate of `kernel` against the SMs' issue peak
+    (4 schedulers per SM, one warp instruction per scheduler per cycle, at
+    the SM clock sampled during the timed region), and its SIMT efficiency
+    (threads per warp instruction / 32, the divergence figure)."""
+    k = profiled(kernel, hits)
+    if k is None or "warp_inst" not in k or not sm_mhz:
+        return None
+    achieved = k["warp_inst"] / (kernel_ms / 1e3) / 1e9
+    peak = 4 * sm_count * sm_mhz / 1e3
+    return {"warp_inst": k["warp_inst"], "achieved_ginst_s": achieved, "peak_ginst_s": peak,
+            "frac": achieved / peak, "sm_mhz": sm_mhz,
+            "simt_efficiency": k["thread_inst"] / (32.0 * k["warp_inst"])}
 
 
 def peaks():
@@ -337,6 +361,8 @@ def main():
                  + 4 * H + 21 * T + 12 * ev.n_events)
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kms[2] / 1e3) / 1e9
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
     # the sort kernel streams the inputs (16 B per hit) and writes the sorted hits (18 B per hit)
     sort_bytes = 16 * ev.n_hits + 4 * (ev.n_events + 1) + 18 * ev.n_hits + 4 * 54 * ev.n_events
     sort_gbs = sort_bytes / (kms[1] / 1e3) / 1e9
@@ -420,7 +446,7 @@ def main():
         fp16 = {"value": ev.n_events / (hms / 1e3), "unit": "events/s", "ms_per_step": hms,
                 "speedup": ms / hms, "tracks": int(hout.counts[0].item()), "tracks_fp32": T,
                 "kernel_ms": {"sort": hk[1], "search": hk[2]},
-                "search_traffic": profiled_traffic("k_search_persistent_fp16", ev.n_hits)}
+                "search_traffic": profiled_traffic(f"k_search_persistent_fp16<{threads}>", ev.n_hits)}
         hh.close()
         del hout
         torch.cuda.empty_cache()
@@ -532,14 +558,17 @@ def main():
             "e2e": e2e,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": profiled_traffic("k_search_persistent", ev.n_hits),
-                         "traffic_source": "single-pass ncu capture of the full-size launch (profiles/traffic.json)",
+                         "traffic": profiled_traffic(f"k_search_persistent<{threads}>", ev.n_hits),
+                         "traffic_source": "single-pass ncu capture of the full-size launch at this block size (profiles/traffic.json)",
                          "peak_kind": peak_kind,
                          "kernel": "k_search_persistent", "kernel_ms": kms[2],
                          "kernel_ms_all": {"order": kms[0], "sort": kms[1], "search": kms[2],
                                            "scan": kms[3], "consolidate": kms[4]},
                          "sort_kernel": {"achieved_gbs": sort_gbs, "frac": sort_gbs / peak,
-                                         "traffic": profiled_traffic("k_sort", ev.n_hits)}},
+                                         "traffic": profiled_traffic("k_sort", ev.n_hits),
+                                         "issue": issue_roofline("k_sort", ev.n_hits, kms[1], sm_mhz, sm_count)},
+                         "issue": issue_roofline(f"k_search_persistent<{threads}>", ev.n_hits, kms[2], sm_mhz,
+                                                 sm_count)},
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clk,
