@@ -268,7 +268,7 @@ typedef struct {
     const int32_t* track_hits;
     const float* params;     /* [n_tracks * 4] */
     const float* chi2;
-    double latency_s;        /* submit -> done */
+    double latency_s;        /* submit (scheduled arrival for sbt_server_submit_schedule) -> done */
 } sbt_result;
 
 /* memory_budget_bytes bounds the device memory of in-flight events (inputs,
@@ -283,7 +283,8 @@ sbt_status sbt_server_submit(sbt_server* s, int64_t request_id, const float* x, 
 
 /* Open-loop load generator: a native thread submits event e of the host batch
  * (x, y, z, module [event_offsets[e] .. event_offsets[e+1])) arrival_s[e]
- * seconds after this call, with request id first_id + e.  The call copies the
+ * seconds after this call, with request id first_id + e; its latency counts
+ * from that scheduled time.  The call copies the
  * batch into pinned host memory (uploads of consecutive events then need no
  * further copy) and returns at once; results arrive through
  * sbt_server_poll or sbt_server_drain. */
@@ -309,7 +310,10 @@ sbt_status sbt_server_drain(sbt_server* s, int64_t* ids, int32_t* status, double
 sbt_status sbt_server_release(sbt_server* s, int64_t request_id);
 
 /* stats (host, 8 doubles): completed, submitted, batches launched, mean
- * events per batch, peak device bytes in flight, failed batches, 0, 0. */
+ * events per batch, peak device bytes in flight, failed batches, the largest
+ * delay (seconds) of the latest open-loop schedule's generator behind that
+ * schedule, and the launcher thread's total time (seconds) spent enqueueing
+ * batches (copies, kernels, downloads). */
 sbt_status sbt_server_stats(sbt_server* s, double* stats);
 
 /* Makes the next launched batch fail on the host side (test hook for the

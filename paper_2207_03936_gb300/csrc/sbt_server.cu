@@ -84,9 +84,24 @@ struct HostBuf {
 };
 
 // Pinned copy of a scheduled batch.
+// Pinned host copy of a scheduled batch (x, y, z, module of `cap` hits).
+// Batches are pooled by the server: the last request that refers to one
+// returns it to the pool (freeing gigabytes of pinned memory takes tens of
+// milliseconds, which would hold up the results being published), and the
+// next schedule reuses it when it is large enough.
 struct PinnedBatch {
     float *x = nullptr, *y = nullptr, *z = nullptr;
     int32_t* m = nullptr;
+    size_t cap = 0;
+    bool alloc(size_t hits)
+    {
+        const size_t nb = sizeof(float) * std::max<size_t>(hits, 1);
+        if (cudaMallocHost(&x, nb) != cudaSuccess || cudaMallocHost(&y, nb) != cudaSuccess ||
+            cudaMallocHost(&z, nb) != cudaSuccess || cudaMallocHost(&m, nb) != cudaSuccess)
+            return false;
+        cap = std::max<size_t>(hits, 1);
+        return true;
+    }
     ~PinnedBatch()
     {
         if (x) cudaFreeHost(x);
@@ -169,12 +184,14 @@ struct sbt_server {
     std::map<int64_t, Materialized> polled;
     std::vector<ResultBlock*> free_blocks;
     std::vector<std::unique_ptr<ResultBlock>> all_blocks;
+    std::vector<std::unique_ptr<PinnedBatch>> pinned_pool;  // batches no request refers to
     std::atomic<bool> stop{false};
     std::atomic<bool> launcher_done{false};
     std::atomic<bool> inject{false};
     int64_t in_flight_bytes = 0;
     double st_completed = 0, st_submitted = 0, st_batches = 0, st_events_batched = 0,
-           st_peak_bytes = 0, st_failed = 0;
+           st_peak_bytes = 0, st_failed = 0, st_feed_lag = 0;
+    std::atomic<double> st_launch_s{0.0};  // launcher time spent enqueueing batches
     std::thread launcher, harvester, feeder;
 };
 
@@ -313,12 +330,15 @@ void launcher_loop(sbt_server* S)
         sl.bytes = bytes;
         sl.block = block;
         sl.failed = false;
+        const double tl = now_s();
         if (S->inject.exchange(false)) {
             sl.failed = true;  // host-side failure: nothing was enqueued
         } else if (!launch_batch(sl)) {
             cudaStreamSynchronize(sl.stream);  // drain what was enqueued before reuse
             sl.failed = true;
         }
+        S->st_launch_s.store(S->st_launch_s.load(std::memory_order_relaxed) + (now_s() - tl),
+                             std::memory_order_relaxed);
         sl.busy.store(true, std::memory_order_release);
     }
     S->launcher_done.store(true);
@@ -473,12 +493,31 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
     if (!S || n_events < 0 || !event_offsets || !arrival_s) return SBT_ERR_ARG;
     if (S->stop.load()) return SBT_ERR_STATE;
     if (S->feeder.joinable()) S->feeder.join();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->st_feed_lag = 0.0;
+    }
     const int32_t H = event_offsets[n_events];
-    auto batch = std::make_shared<PinnedBatch>();
-    const size_t nb = sizeof(float) * (size_t)std::max(H, 1);
-    if (cudaMallocHost(&batch->x, nb) != cudaSuccess || cudaMallocHost(&batch->y, nb) != cudaSuccess ||
-        cudaMallocHost(&batch->z, nb) != cudaSuccess || cudaMallocHost(&batch->m, nb) != cudaSuccess)
-        return SBT_ERR_CUDA;
+    std::unique_ptr<PinnedBatch> pb;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto it = S->pinned_pool.begin(); it != S->pinned_pool.end(); ++it)
+            if ((*it)->cap >= (size_t)std::max(H, 1)) {
+                pb = std::move(*it);
+                S->pinned_pool.erase(it);
+                break;
+            }
+    }
+    if (!pb) {
+        pb.reset(new PinnedBatch());
+        if (!pb->alloc((size_t)H)) return SBT_ERR_CUDA;
+    }
+    // the last request holding the batch hands it back to the pool (never
+    // under the server lock: requests are released outside it)
+    std::shared_ptr<PinnedBatch> batch(pb.release(), [S](PinnedBatch* b) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->pinned_pool.emplace_back(b);
+    });
     if (H) {
         std::memcpy(batch->x, x, sizeof(float) * H);
         std::memcpy(batch->y, y, sizeof(float) * H);
@@ -489,6 +528,8 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
     std::vector<double> at(arrival_s, arrival_s + n_events);
     S->feeder = std::thread([S, batch, vo = std::move(vo), at = std::move(at), first_id, n_events]() {
         const auto t0 = Clock::now();
+        const double t0_s = std::chrono::duration<double>(t0.time_since_epoch()).count();
+        double lag = 0.0;
         auto due_at = [&](int32_t e) {
             return t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(at[e]));
         };
@@ -504,6 +545,9 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
             std::vector<Request> due;
             const double ts = now_s();
             while (e < n_events && due_at(e) <= now) {
+                // latency counts from the scheduled arrival, so a feeder
+                // running late shows in it rather than hiding a backlog
+                lag = std::max(lag, ts - (t0_s + at[e]));
                 Request r;
                 r.id = first_id + e;
                 const int32_t lo = vo[e];
@@ -514,7 +558,7 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
                 r.n = vo[e + 1] - lo;
                 r.pinned = true;
                 r.hold = batch;
-                r.t_submit = ts;
+                r.t_submit = t0_s + at[e];
                 due.push_back(std::move(r));
                 e++;
             }
@@ -522,6 +566,7 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
                 std::lock_guard<std::mutex> lk(S->mu);
                 for (auto& r : due) S->pending.push_back(std::move(r));
                 S->st_submitted += (double)due.size();
+                S->st_feed_lag = lag;
             }
             S->cv_work.notify_one();
         }
@@ -629,8 +674,8 @@ sbt_status sbt_server_stats(sbt_server* S, double* stats)
     stats[3] = S->st_batches > 0 ? S->st_events_batched / S->st_batches : 0.0;
     stats[4] = S->st_peak_bytes;
     stats[5] = S->st_failed;
-    stats[6] = 0.0;
-    stats[7] = 0.0;
+    stats[6] = S->st_feed_lag;
+    stats[7] = S->st_launch_s.load(std::memory_order_relaxed);
     return SBT_OK;
 }
 
@@ -649,6 +694,10 @@ sbt_status sbt_server_destroy(sbt_server* S)
     S->cv_work.notify_all();
     if (S->launcher.joinable()) S->launcher.join();
     if (S->harvester.joinable()) S->harvester.join();
+    // every request is gone before the pinned batches they refer to
+    S->pending.clear();
+    for (auto& up : S->slots) up->reqs.clear();
+    S->pinned_pool.clear();
     for (auto& up : S->slots) {
         Slot& sl = *up;
         cudaStreamSynchronize(sl.stream);

@@ -448,7 +448,8 @@ class Server:
         v = (ctypes.c_double * 8)()
         _check(self.L.sbt_server_stats(self.s, v))
         return {"completed": v[0], "submitted": v[1], "batches": v[2], "mean_batch_events": v[3],
-                "peak_bytes": v[4], "failed_batches": v[5]}
+                "peak_bytes": v[4], "failed_batches": v[5], "feed_lag_s": v[6],
+                "launch_busy_s": v[7]}
 
     def inject_failure(self):
         _check(self.L.sbt_server_inject_failure(self.s))

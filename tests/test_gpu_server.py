@@ -38,6 +38,7 @@ def test_served_results_equal_results_alone():
         h.close()
     assert len(got) == ev.n_events
     assert st["batches"] > 1 and st["peak_bytes"] <= 64 << 20
+    assert 0.0 <= st["feed_lag_s"] < 1.0 and st["launch_busy_s"] > 0.0
     for e in range(ev.n_events):
         lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
         one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], ev.module_z)
@@ -107,3 +108,33 @@ def test_served_results_keep_storage_and_event_cut_settings():
         assert np.array_equal(r.hit_offsets, one.hit_offsets)
         assert np.array_equal(r.track_hits, one.track_hits)
         assert np.array_equal(r.params.view(np.uint32), one.params.view(np.uint32))
+
+
+def test_consecutive_schedules_reuse_the_pinned_batch():
+    """A second open-loop schedule on the same server takes the pinned host
+    batch the first one returned to the pool (smaller, so it fits) and serves
+    the same results as each event alone."""
+    from paper_2207_03936_gb300 import sbt
+    ev1 = synth.make_events(2, 80, seed=1, workers=1)
+    ev2 = synth.make_events(2, 40, seed=2, workers=1)
+    h = sbt.sbt_create(ev1.module_z, sbt.default_config())
+    srv = sbt.Server(h, memory_budget_bytes=64 << 20, max_streams=3, max_batch_events=16)
+    try:
+        srv.submit_schedule(ev1, np.zeros(ev1.n_events))
+        got1 = collect(srv, ev1.n_events)
+        srv.submit_schedule(ev2, synth.poisson_arrivals(50000.0, ev2.n_events, seed=5), first_id=1000)
+        got2 = collect(srv, ev2.n_events)
+    finally:
+        srv.close()
+        h.close()
+    assert sorted(got1) == list(range(ev1.n_events))
+    assert sorted(got2) == list(range(1000, 1000 + ev2.n_events))
+    for ev, got, base in ((ev1, got1, 0), (ev2, got2, 1000)):
+        for e in range(ev.n_events):
+            lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+            one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], ev.module_z)
+            r = got[base + e]
+            assert r.status == 0
+            assert np.array_equal(r.hit_offsets, one.hit_offsets)
+            assert np.array_equal(r.track_hits, one.track_hits)
+            assert np.array_equal(r.params, one.params)
