@@ -423,3 +423,45 @@ def test_autotune_keeps_results(sbt):
         assert_same(run_gpu(sbt, h, ev, True), oracle_of(ev))
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("fp16", [0, 1])
+def test_maximum_event_size_bit_exact(sbt, fp16):
+    """An event of exactly the largest supported size (16384 hits: the sort's
+    shared-memory buffers and the 16-bit hit positions of the search) between
+    two ordinary events, through the plain, batched and host entry points; an
+    event one hit larger is reported as SBT_ERR_CAPACITY, the others kept."""
+    base = synth.make_events(2, 14, seed=4, workers=1)
+    o = base.event_offsets
+    big = slice(int(o[1]), int(o[1]) + 16384)          # events 1.. merged, cut at 16384 hits
+    assert o[13] - o[1] > 16384
+    parts = [slice(int(o[0]), int(o[1])), big, slice(int(o[13]), int(o[14]))]
+    cat = lambda a: np.concatenate([a[p] for p in parts])
+    sizes = [p.stop - p.start for p in parts]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    ev = synth.Events(cat(base.x), cat(base.y), cat(base.z), cat(base.module), offs,
+                      cat(base.mc), 0, base.module_z)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(max_hits_per_event=16384, fp16_hits=fp16, **CFG))
+    try:
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                                 oracle.config(**CFG), fp16_hits=bool(fp16))
+        assert ref.status[1] == 0 and ref.n_tracks > 0
+        assert_same(run_gpu(sbt, h, ev, False), ref)
+        assert_same(run_gpu(sbt, h, ev, True), ref)
+        host = [torch.from_numpy(a) for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+        assert_same(sbt.sbt_reconstruct_host(h, *host).compact(), ref)
+        # one more hit in the middle event: that event alone is refused
+        extra = slice(big.start, big.stop + 1)
+        parts2 = [parts[0], extra, parts[2]]
+        cat2 = lambda a: np.concatenate([a[p] for p in parts2])
+        offs2 = np.array([0, sizes[0], sizes[0] + 16385, sizes[0] + 16385 + sizes[2]], np.int32)
+        ev2 = synth.Events(cat2(base.x), cat2(base.y), cat2(base.z), cat2(base.module), offs2,
+                           cat2(base.mc), 0, base.module_z)
+        for b in (False, True):
+            g = run_gpu(sbt, h, ev2, b)
+            assert list(g["event_status"]) == [0, sbt.SBT_ERR_CAPACITY, 0]
+            assert g["track_offsets"][1] == g["track_offsets"][2]
+            assert g["track_offsets"][1] == ref.track_offsets[1]
+            assert g["track_offsets"][3] - g["track_offsets"][2] == ref.track_offsets[3] - ref.track_offsets[2]
+    finally:
+        h.close()
