@@ -3,13 +3,14 @@
 A step reconstructs one batch of synthetic events (100k uneven events, pileup
 U(1, 20), 200-12600 hits each; inputs larger than L2) through the batched C
 entry point (persistent work-queue kernel replayed from a CUDA graph).  The
-line also reports the plain one-block-per-event launch on the same batch,
-the same batch traversed in ascending z (module order reversed) and with the
-global event cut (busiest 10% of events rejected) and with fp16 hit
-storage, the
-end-to-end host entry point (copies inside the timed region), the alignment
-adjoint, the dominant kernel's roofline fraction, the SM clocks
-seen during the timed region and the CPU oracle timed on host cores over a
+line also reports the plain one-block-per-event launch on the same batch;
+the same batch traversed in ascending z (module order reversed), with the
+global event cut (busiest 10% of events rejected) and with fp16 hit storage;
+the end-to-end host entry point (copies inside the timed region); the
+continuous-batching server under open-loop arrivals; the alignment adjoint;
+the dominant kernel's HBM and issue roofline fractions (DRAM bytes and
+instruction counts from the committed full-size ncu capture); the SM clocks
+seen during the timed region; and the CPU oracle timed on host cores over a
 bounded sample, whose tracks are compared with the GPU's event by event.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
