@@ -80,16 +80,19 @@ def lib() -> ctypes.CDLL:
                                      _f32p, ctypes.POINTER(ctypes.c_float)]
         L.sbt_oracle_event.restype = ctypes.c_int32
         L.sbt_oracle_event.argtypes = [_f32p, _f32p, _f32p, _i32p, ctypes.c_int32, _f32p,
-                                       ctypes.c_int32, ctypes.POINTER(Config), _i32p, _i32p,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Config),
+                                       _i32p, _i32p,
                                        _f32p, _f32p, _i32p, _i32p]
         L.sbt_oracle_batch.restype = ctypes.c_int32
         L.sbt_oracle_batch.argtypes = [_f32p, _f32p, _f32p, _i32p, _i32p, ctypes.c_int32, _f32p,
-                                       ctypes.c_int32, ctypes.POINTER(Config), ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Config),
+                                       ctypes.c_int32,
                                        _i32p, _i32p, _i32p, _i32p, _i32p, _f32p, _f32p, _i32p,
                                        _i32p]
         L.sbt_oracle_seed_step.restype = ctypes.c_int32
         L.sbt_oracle_seed_step.argtypes = [_f32p, _f32p, _f32p, _i32p, ctypes.c_int32, _f32p,
-                                           ctypes.c_int32, ctypes.POINTER(Config), ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Config),
+                                           ctypes.c_int32,
                                            ctypes.c_void_p, _i32p, _i32p, _i32p]
         L.sbt_oracle_align_chi2.restype = ctypes.c_double
         L.sbt_oracle_align_chi2.argtypes = [_f32p, _f32p, _f32p, _i32p, _i32p, _i32p,
@@ -105,6 +108,17 @@ def _f32(a):
 
 def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _second_planes(module_z2, M: int):
+    """(array kept alive, pointer) of the second plane positions of module
+    pairs, or (None, None) for single planes."""
+    if module_z2 is None:
+        return None, None
+    z2 = _f32(module_z2)
+    if z2.shape != (M,):
+        raise ValueError("module_z2 must have one entry per module")
+    return z2, z2.ctypes.data
 
 
 def atan2(y: float, x: float) -> float:
@@ -162,10 +176,12 @@ class Tracks:
         return int(self.hit_offsets.shape[0] - 1)
 
 
-def event(x, y, z, module, module_z, cfg: Config | None = None):
-    """Reconstruct one event; hit indices are local to the event."""
+def event(x, y, z, module, module_z, cfg: Config | None = None, module_z2=None):
+    """Reconstruct one event; hit indices are local to the event.  module_z2:
+    second plane of each module pair (hits with x < 0), None for single planes."""
     cfg = cfg or config()
     x, y, z, module, module_z = _f32(x), _f32(y), _f32(z), _i32(module), _f32(module_z)
+    z2, z2p = _second_planes(module_z2, module_z.shape[0])
     n = x.shape[0]
     cap = max(n, 1)
     tl = np.empty(cap, np.int32)
@@ -174,8 +190,8 @@ def event(x, y, z, module, module_z, cfg: Config | None = None):
     c2 = np.empty(cap, np.float32)
     nd = np.empty(cap, np.int32)
     st = np.zeros(8, np.int32)
-    nt = lib().sbt_oracle_event(x, y, z, module, n, module_z, module_z.shape[0], ctypes.byref(cfg),
-                                tl, th, pr, c2, nd, st)
+    nt = lib().sbt_oracle_event(x, y, z, module, n, module_z, z2p, module_z.shape[0],
+                                ctypes.byref(cfg), tl, th, pr, c2, nd, st)
     if nt < 0:
         raise ValueError("invalid event")
     h = int(tl[:nt].sum())
@@ -193,15 +209,18 @@ def round_fp16(a) -> np.ndarray:
 
 
 def reconstruct(x, y, z, module, event_offsets, module_z, cfg: Config | None = None,
-                n_threads: int | None = None, fp16_hits: bool = False) -> Tracks:
+                n_threads: int | None = None, fp16_hits: bool = False, module_z2=None) -> Tracks:
     """Reconstruct a batch of events on host threads; returns CSR tracks.
     With fp16_hits the hit coordinates are first rounded to fp16, as the
-    fp16 hit-storage mode keeps them; everything after is unchanged."""
+    fp16 hit-storage mode keeps them; everything after is unchanged.
+    module_z2: second plane of each module pair (hits with x < 0), None for
+    single planes."""
     cfg = cfg or config()
     x, y, z, module = _f32(x), _f32(y), _f32(z), _i32(module)
     if fp16_hits:
         x, y, z = round_fp16(x), round_fp16(y), round_fp16(z)
     eo, module_z = _i32(event_offsets), _f32(module_z)
+    z2, z2p = _second_planes(module_z2, module_z.shape[0])
     E = eo.shape[0] - 1
     H = int(eo[-1]) if E >= 0 else 0
     if n_threads is None:
@@ -216,8 +235,8 @@ def reconstruct(x, y, z, module, event_offsets, module_z, cfg: Config | None = N
     sc = np.zeros(tcap, np.float32)
     sn = np.zeros(tcap, np.int32)
     ss = np.zeros(8 * max(E, 1), np.int32)
-    lib().sbt_oracle_batch(x, y, z, module, eo, E, module_z, module_z.shape[0], ctypes.byref(cfg),
-                           int(n_threads), ntr, nh, st, sl, sh, sp, sc, sn, ss)
+    lib().sbt_oracle_batch(x, y, z, module, eo, E, module_z, z2p, module_z.shape[0],
+                           ctypes.byref(cfg), int(n_threads), ntr, nh, st, sl, sh, sp, sc, sn, ss)
     ntr, nh, st = ntr[:E], nh[:E], st[:E]
     to = np.zeros(E + 1, np.int32)
     np.cumsum(ntr, out=to[1:])
@@ -236,15 +255,17 @@ def reconstruct(x, y, z, module, event_offsets, module_z, cfg: Config | None = N
                   st, ss[:8 * E].reshape(E, 8))
 
 
-def seed_step(x, y, z, module, module_z, s: int, cfg: Config | None = None, flags=None):
+def seed_step(x, y, z, module, module_z, s: int, cfg: Config | None = None, flags=None,
+              module_z2=None):
     """Seeds of seeding step s as (a, c, b) sorted positions, ordered by c."""
     cfg = cfg or config()
     x, y, z, module, module_z = _f32(x), _f32(y), _f32(z), _i32(module), _f32(module_z)
+    z2, z2p = _second_planes(module_z2, module_z.shape[0])
     n = x.shape[0]
     cap = max(n, 1)
     oa, oc, ob = (np.empty(cap, np.int32) for _ in range(3))
     fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
-    cnt = lib().sbt_oracle_seed_step(x, y, z, module, n, module_z, module_z.shape[0],
+    cnt = lib().sbt_oracle_seed_step(x, y, z, module, n, module_z, z2p, module_z.shape[0],
                                      ctypes.byref(cfg), int(s),
                                      fl.ctypes.data if fl is not None else None, oa, oc, ob)
     if cnt < 0:

@@ -48,6 +48,14 @@
  *      fp32 sums in hit order, chi2 = sum of squared residuals / sigma^2.
  *   R9 output: tracks sorted by their smallest input hit index, hits of a
  *      track in traversal (module) order.
+ *   R10 module pairs (the paper works on module pairs and calls them modules,
+ *      section "Search by triplet"; its VELO has modules on two sides of the
+ *      beam, Fig. 2): when a second plane position module_z2[m] is given,
+ *      module m is a pair of one-sided planes, hits with x >= 0 on the plane
+ *      at module_z[m] and hits with x < 0 on the plane at module_z2[m].  Every
+ *      extrapolation to a module (R4, R5) targets the plane of the hit it is
+ *      compared with, so a candidate's scatter is measured at its own plane.
+ *      Without module_z2 every module is one plane at module_z[m].
  *
  * Arithmetic: fp32, every operation rounded as written (build with
  * -ffp-contract=off, no fast-math); IEEE division and rounding.
@@ -217,6 +225,7 @@ typedef struct {
 typedef struct {
     int32_t n, M;
     const float* module_z;
+    const float* module_z2; /* second plane of each module pair (x < 0), or NULL */
     const sbt_oracle_config* cfg;
     float *sx, *sy, *sz;
     uint16_t* sphi;
@@ -248,6 +257,13 @@ static void extrapolate(const or_event* E, int32_t a, int32_t c, float zt, float
     float tz = (zt - E->sz[c]) / dz;
     *xp = E->sx[c] + (E->sx[c] - E->sx[a]) * tz;
     *yp = E->sy[c] + (E->sy[c] - E->sy[a]) * tz;
+}
+
+/* R10: z of the plane that holds hit b (sorted position) of module m. */
+static float plane_z(const or_event* E, int32_t m, int32_t b)
+{
+    if (E->module_z2 && E->sx[b] < 0.0f) return E->module_z2[m];
+    return E->module_z[m];
 }
 
 static float scatter(const or_event* E, int32_t b, float xp, float yp)
@@ -285,14 +301,13 @@ static int seed_for(or_event* E, int32_t s, int32_t c, int32_t* oa, int32_t* ob)
     int found = 0;
     float best_sc = 0.0f;
     int32_t best_a = -1, best_b = -1;
-    const float zi = E->module_z[i];
     for (int32_t a = o0; a < o1; a++) {
         if (E->flag[a]) continue;
         if (nunf > K && sbt_oracle_phi_distance(E->sphi[a], E->sphi[c]) > dmax) continue;
-        float xp, yp;
-        extrapolate(E, a, c, zi, &xp, &yp);
         for (int32_t b = i0; b < i1; b++) {
             if (E->flag[b]) continue;
+            float xp, yp;
+            extrapolate(E, a, c, plane_z(E, i, b), &xp, &yp);
             float sc = scatter(E, b, xp, yp);
             if (!(sc < E->cfg->max_scatter_seed)) continue;
             int better = !found || sc < best_sc ||
@@ -319,7 +334,7 @@ static int seed_for(or_event* E, int32_t s, int32_t c, int32_t* oa, int32_t* ob)
  * that the tests can compare it with exhaustive enumeration.
  */
 int32_t sbt_oracle_seed_step(const float* x, const float* y, const float* z, const int32_t* module,
-                             int32_t n, const float* module_z, int32_t M,
+                             int32_t n, const float* module_z, const float* module_z2, int32_t M,
                              const sbt_oracle_config* cfg, int32_t s, const uint8_t* flags,
                              int32_t* out_a, int32_t* out_c, int32_t* out_b)
 {
@@ -329,6 +344,7 @@ int32_t sbt_oracle_seed_step(const float* x, const float* y, const float* z, con
     E.n = n;
     E.M = M;
     E.module_z = module_z;
+    E.module_z2 = module_z2;
     E.cfg = cfg;
     size_t nn = (size_t)(n > 0 ? n : 1);
     E.perm = (int32_t*)malloc(sizeof(int32_t) * nn);
@@ -387,7 +403,6 @@ static uint64_t claim_key(float score, int32_t key)
 static void follow(or_event* E, int32_t t)
 {
     const int32_t t0 = E->modoff[t], t1 = E->modoff[t + 1];
-    const float zt = E->module_z[t];
     /* candidates */
     for (int32_t ti = 0; ti < E->npool; ti++) {
         or_track* T = &E->pool[ti];
@@ -396,10 +411,10 @@ static void follow(or_event* E, int32_t t)
         if (T->nhits == 3 &&
             (E->flag[T->hit[0]] || E->flag[T->hit[1]] || E->flag[T->hit[2]]))
             continue;
-        float xp, yp;
-        extrapolate(E, T->hit[T->nhits - 2], T->hit[T->nhits - 1], zt, &xp, &yp);
         for (int32_t b = t0; b < t1; b++) {
             if (E->flag[b]) continue;
+            float xp, yp;
+            extrapolate(E, T->hit[T->nhits - 2], T->hit[T->nhits - 1], plane_z(E, t, b), &xp, &yp);
             float sc = scatter(E, b, xp, yp);
             if (!(sc < E->cfg->max_scatter_follow)) continue;
             if (T->cand < 0 || sc < T->cand_sc) {  /* b ascending: ties keep the smaller */
@@ -511,14 +526,16 @@ static int cmp_out(const void* a, const void* b)
 
 /*
  * Reconstruct one event.  Inputs: n hits (x, y, z, module id in traversal
- * order), module_z[M] plane positions.  Outputs, each with capacity n:
+ * order), module_z[M] plane positions and, for module pairs (R10), the
+ * second planes module_z2[M] (NULL: single planes).  Outputs, each with
+ * capacity n:
  * track_len[t], track_hits (concatenated input indices of the event),
  * params[4 t], chi2[t], ndof[t].  stats (8 ints, may be NULL): seeds,
  * tracklets, accepted tracklets, tracks (>= 4 hits), max alive forming tracks.
  * Returns the number of tracks or -1 on invalid input.
  */
 int32_t sbt_oracle_event(const float* x, const float* y, const float* z, const int32_t* module,
-                         int32_t n, const float* module_z, int32_t M,
+                         int32_t n, const float* module_z, const float* module_z2, int32_t M,
                          const sbt_oracle_config* cfg, int32_t* track_len, int32_t* track_hits,
                          float* params, float* chi2, int32_t* ndof, int32_t* stats)
 {
@@ -528,6 +545,7 @@ int32_t sbt_oracle_event(const float* x, const float* y, const float* z, const i
     E.n = n;
     E.M = M;
     E.module_z = module_z;
+    E.module_z2 = module_z2;
     E.cfg = cfg;
     size_t nn = (size_t)(n > 0 ? n : 1);
     E.perm = (int32_t*)malloc(sizeof(int32_t) * nn);
@@ -647,6 +665,7 @@ typedef struct {
     const int32_t* event_offsets;
     int32_t n_events;
     const float* module_z;
+    const float* module_z2;
     int32_t M;
     const sbt_oracle_config* cfg;
     int32_t* ev_ntracks;
@@ -674,7 +693,7 @@ static void* batch_worker(void* arg)
         int32_t n = J->event_offsets[e + 1] - off;
         int32_t tslot = off / 3;
         int32_t nt = sbt_oracle_event(J->x + off, J->y + off, J->z + off, J->module + off, n,
-                                      J->module_z, J->M, J->cfg, J->slot_len + tslot,
+                                      J->module_z, J->module_z2, J->M, J->cfg, J->slot_len + tslot,
                                       J->slot_hits + off, J->slot_params + 4 * (int64_t)tslot,
                                       J->slot_chi2 + tslot, J->slot_ndof + tslot,
                                       J->ev_stats ? J->ev_stats + 8 * (int64_t)e : NULL);
@@ -704,7 +723,8 @@ static void* batch_worker(void* arg)
  */
 int32_t sbt_oracle_batch(const float* x, const float* y, const float* z, const int32_t* module,
                          const int32_t* event_offsets, int32_t n_events, const float* module_z,
-                         int32_t M, const sbt_oracle_config* cfg, int32_t n_threads,
+                         const float* module_z2, int32_t M, const sbt_oracle_config* cfg,
+                         int32_t n_threads,
                          int32_t* ev_ntracks, int32_t* ev_nhits, int32_t* ev_status,
                          int32_t* slot_len, int32_t* slot_hits, float* slot_params,
                          float* slot_chi2, int32_t* slot_ndof, int32_t* ev_stats)
@@ -712,7 +732,7 @@ int32_t sbt_oracle_batch(const float* x, const float* y, const float* z, const i
     batch_job J;
     memset(&J, 0, sizeof(J));
     J.x = x; J.y = y; J.z = z; J.module = module; J.event_offsets = event_offsets;
-    J.n_events = n_events; J.module_z = module_z; J.M = M; J.cfg = cfg;
+    J.n_events = n_events; J.module_z = module_z; J.module_z2 = module_z2; J.M = M; J.cfg = cfg;
     J.ev_ntracks = ev_ntracks; J.ev_nhits = ev_nhits; J.ev_status = ev_status;
     J.slot_len = slot_len; J.slot_hits = slot_hits; J.slot_params = slot_params;
     J.slot_chi2 = slot_chi2; J.slot_ndof = slot_ndof; J.ev_stats = ev_stats;

@@ -26,6 +26,18 @@ stand in for it):
 * hits are shuffled within each event (the reconstruction must not depend
   on input order beyond its stated tie-breaks).
 
+Module-pair geometry (``pairs=True``; the paper's VELO has its modules on two
+sides of the beam, Fig. 2, and the method works on module pairs, section
+"Search by triplet").  The 52 planes stay where they are, but each covers one
+side only: plane k (ascending z) records hits with x >= 0 when k is even and
+x < 0 when k is odd (decided on the measured x; hits within 1 um of x = 0
+are dropped so that the sign of a stored coordinate always names its plane).
+Planes 2q and 2q + 1 form module pair q; the algorithm sees 26 modules (pair
+ids in traversal order, 0 = the pair furthest from the interaction point)
+and takes each pair's two plane positions, ``module_z`` for its x >= 0 plane
+and ``module_z2`` for its x < 0 plane.  A straight track thus leaves one hit
+per pair, about 41 mm apart.
+
 Random numbers come from numpy's PCG64 with a fixed seed; events are drawn
 in fixed chunks so the result does not depend on the machine.
 """
@@ -37,6 +49,7 @@ import math
 import numpy as np
 
 N_MODULES = 52
+N_PAIRS = N_MODULES // 2
 R_MIN = 5.1
 R_MAX = 42.0
 Z_FIRST = -290.0
@@ -71,6 +84,7 @@ class Events:
     mc: np.ndarray
     n_particles: int
     module_z: np.ndarray
+    module_z2: np.ndarray | None = None   # second plane of each module pair (x < 0 side)
 
     @property
     def n_events(self) -> int:
@@ -92,7 +106,7 @@ class Events:
         return Events(self.x[sl].copy(), self.y[sl].copy(), self.z[sl].copy(),
                       self.module[sl].copy(),
                       (self.event_offsets[first:first + count + 1] - lo).astype(np.int32),
-                      mc, self.n_particles, self.module_z)
+                      mc, self.n_particles, self.module_z, self.module_z2)
 
 
 @dataclasses.dataclass
@@ -109,6 +123,7 @@ class Recipe:
     smear: float = 0.012            # mm
     noise_frac: float = 0.01
     misalign: bool = False
+    pairs: bool = False             # module-pair geometry (two one-sided planes per module)
     seed: int = 0
 
 
@@ -233,6 +248,10 @@ def _chunk(rng: np.random.Generator, rec: Recipe, n_ev: int, zasc: np.ndarray):
     keep &= rng.uniform(size=tot) < rec.hit_eff
     sx = rng.normal(0.0, rec.smear, size=tot)
     sy = rng.normal(0.0, rec.smear, size=tot)
+    if rec.pairs:
+        # one-sided planes: even planes see x >= 0, odd planes x < 0 (measured x)
+        mx = xt + sx
+        keep &= np.where(k % 2 == 0, mx >= 1.0e-3, mx <= -1.0e-3)
     hx = (xt + sx)[keep]
     hy = (yt + sy)[keep]
     hz = zk[keep]
@@ -247,7 +266,11 @@ def _chunk(rng: np.random.Generator, rec: Recipe, n_ev: int, zasc: np.ndarray):
     nk_ = rng.integers(0, N_MODULES, size=nn)
     nr = np.sqrt(rng.uniform(R_MIN * R_MIN, R_MAX * R_MAX, size=nn))
     nphi = rng.uniform(0.0, 2.0 * math.pi, size=nn)
-    ax = np.concatenate([hx, nr * np.cos(nphi)])
+    nx = nr * np.cos(nphi)
+    if rec.pairs:
+        # noise on a one-sided plane lies on its side
+        nx = np.where(nk_ % 2 == 0, 1.0, -1.0) * np.maximum(np.abs(nx), 1.0e-3)
+    ax = np.concatenate([hx, nx])
     ay = np.concatenate([hy, nr * np.sin(nphi)])
     az = np.concatenate([hz, zasc[nk_]])
     ak = np.concatenate([hk, nk_])
@@ -302,6 +325,8 @@ def generate(rec: Recipe, workers: int | None = None) -> Events:
     k = np.concatenate(ks) if ks else np.zeros(0, dtype=np.int32)
     mc = np.concatenate(mcs) if mcs else np.zeros(0, dtype=np.int32)
     counts = np.concatenate(cnts) if cnts else np.zeros(0, dtype=np.int64)
+    if rec.misalign and rec.pairs:
+        raise ValueError("misalignment is defined for single planes only")
     if rec.misalign:
         # measured position = placement error applied inversely about the plane centre
         th = misalignment(rec.seed)
@@ -314,14 +339,21 @@ def generate(rec: Recipe, workers: int | None = None) -> Events:
     np.cumsum(counts, out=offsets[1:])
     if offsets[-1] >= 2**31:
         raise ValueError("batch exceeds int32 hit indexing")
+    if rec.pairs:
+        module = (N_PAIRS - 1 - k // 2).astype(np.int32)
+        zp = module_z_ascending().reshape(N_PAIRS, 2)[::-1].astype(np.float32)
+        return Events(x.astype(np.float32), y.astype(np.float32), z.astype(np.float32), module,
+                      offsets.astype(np.int32), mc, n_part, zp[:, 0].copy(), zp[:, 1].copy())
     module = (N_MODULES - 1 - k).astype(np.int32)
     return Events(x.astype(np.float32), y.astype(np.float32), z.astype(np.float32), module,
                   offsets.astype(np.int32), mc, n_part, module_z_traversal())
 
 
 def make_events(config: int, n_events: int | None = None, seed: int = 0,
-                workers: int | None = None) -> Events:
-    return generate(recipe_for(config, n_events, seed), workers)
+                workers: int | None = None, pairs: bool = False) -> Events:
+    r = recipe_for(config, n_events, seed)
+    r.pairs = pairs
+    return generate(r, workers)
 
 
 def reverse_traversal(ev: Events) -> Events:
@@ -330,7 +362,8 @@ def reverse_traversal(ev: Events) -> Events:
     and the plane positions are reversed."""
     M = int(ev.module_z.shape[0])
     return Events(ev.x, ev.y, ev.z, (M - 1 - ev.module).astype(np.int32), ev.event_offsets, ev.mc,
-                  ev.n_particles, ev.module_z[::-1].copy())
+                  ev.n_particles, ev.module_z[::-1].copy(),
+                  None if ev.module_z2 is None else ev.module_z2[::-1].copy())
 
 
 def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:

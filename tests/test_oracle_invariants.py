@@ -12,6 +12,7 @@ CFG = dict(k_doublets=4, max_scatter_seed=0.04, max_scatter_follow=0.04,
 
 def check_invariants(ev, res, cfg):
     MZ = ev.module_z
+    MZ2 = ev.module_z2    # module pairs: plane of hits with x < 0
     th, ho = res.track_hits, res.hit_offsets
     # each hit in at most one track
     assert np.bincount(th, minlength=ev.n_hits).max(initial=0) <= 1
@@ -31,7 +32,8 @@ def check_invariants(ev, res, cfg):
             x, y, z = ev.x[h], ev.y[h], ev.z[h]
             for k in range(2, len(h)):
                 dz = np.float32(z[k - 1] - z[k - 2])
-                tz = np.float32(np.float32(MZ[mod[k]] - z[k - 1]) / dz)
+                zt = MZ2[mod[k]] if MZ2 is not None and x[k] < 0 else MZ[mod[k]]
+                tz = np.float32(np.float32(zt - z[k - 1]) / dz)
                 xp = np.float32(x[k - 1] + np.float32(np.float32(x[k - 1] - x[k - 2]) * tz))
                 yp = np.float32(y[k - 1] + np.float32(np.float32(y[k - 1] - y[k - 2]) * tz))
                 dx, dy = np.float32(x[k] - xp), np.float32(y[k] - yp)
