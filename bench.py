@@ -59,6 +59,8 @@ def parse():
                    help="skip the fp16 hit-storage run of the same batch")
     p.add_argument("--no-gec", action="store_true",
                    help="skip the global-event-cut run (busiest 10% of events rejected)")
+    p.add_argument("--no-pairs", action="store_true",
+                   help="skip the module-pair geometry run (one-sided planes paired into 26 modules)")
     p.add_argument("--serving-sweep", action="store_true",
                    help="sweep arrival rate (0.1-1.5x of saturation) and memory budget (2-16 GB)")
     return p.parse_args()
@@ -244,7 +246,7 @@ def cpu_baseline(ev, budget_s: float, gpu_out=None):
         x, y, z, m = (np.concatenate(a) for a in (xs, ys, zs, ms))
         sub_off = np.array(sub_off, np.int32)
         t0 = time.perf_counter()
-        r = oracle.reconstruct(x, y, z, m, sub_off, ev.module_z, n_threads=cores)
+        r = oracle.reconstruct(x, y, z, m, sub_off, ev.module_z, n_threads=cores, module_z2=ev.module_z2)
         t_total += time.perf_counter() - t0
         if gpu_out is not None:
             to, ho, th, prm = (gpu_out["track_offsets"], gpu_out["hit_offsets"], gpu_out["track_hits"],
@@ -311,6 +313,7 @@ def main():
     ev = synth.make_events(3, args.events, seed=rank)
     ev_adj = None if args.no_adjoint else synth.make_events(5)
     ev_srv = None if args.no_serving else synth.make_events(4, 40_000, seed=7)
+    ev_pairs = None if args.no_pairs else synth.make_events(3, args.events, seed=rank, pairs=True)
 
     import torch
     from paper_2207_03936_gb300 import sbt
@@ -461,6 +464,37 @@ def main():
         del hout
         torch.cuda.empty_cache()
 
+    # module-pair geometry: the same pileup with one-sided planes paired into
+    # 26 modules (half the hits per event); the oracle's pair reading checks
+    # a sample of the events
+    pairs = None
+    if ev_pairs is not None:
+        devp = [torch.from_numpy(a).cuda() for a in (ev_pairs.x, ev_pairs.y, ev_pairs.z,
+                                                     ev_pairs.module, ev_pairs.event_offsets)]
+        nmaxp = int(-(-int(np.diff(ev_pairs.event_offsets).max()) // 1024) * 1024)
+        hp = sbt.sbt_create(ev_pairs.module_z,
+                            sbt.default_config(max_hits_per_event=nmaxp, threads_per_block=threads),
+                            module_z2=ev_pairs.module_z2)
+        pout = sbt.TrackOutput.allocate(ev_pairs.n_events, ev_pairs.n_hits)
+        for _ in range(max(1, min(args.warmup, 2))):
+            sbt.sbt_reconstruct_batched(hp, *devp, out=pout)
+        torch.cuda.synchronize()
+        n_p = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(n_p):
+            sbt.sbt_reconstruct_batched(hp, *devp, out=pout)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / n_p
+        pk = sbt.sbt_profile_batched(hp, *devp, pout, reps=2)
+        pres = pout.compact()
+        pairs = {"value": ev_pairs.n_events / (pms / 1e3), "unit": "events/s", "ms_per_step": pms,
+                 "events": ev_pairs.n_events, "hits": ev_pairs.n_hits, "tracks": int(pres["counts"][0]),
+                 "kernel_ms": {"sort": pk[1], "search": pk[2]}, "pres": pres}
+        hp.close()
+        del pout, devp
+        torch.cuda.empty_cache()
+
     # global event cut: the busiest 10% of events rejected unreconstructed;
     # throughput over all input events, physics traded on a truth sample
     gec = None
@@ -550,6 +584,8 @@ def main():
 
     if rank == 0:
         cpu, match = cpu_baseline(ev, args.cpu_seconds, gpu_res)
+        if pairs is not None:
+            _, pairs["match"] = cpu_baseline(ev_pairs, min(args.cpu_seconds, 2.0), pairs.pop("pres"))
         line = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -562,6 +598,7 @@ def main():
             "ascending": ascending,
             "gec": gec,
             "fp16_hits": fp16,
+            "module_pairs": pairs,
             "serving": serving,
             "match": match,
             "adjoint": adj,

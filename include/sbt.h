@@ -52,11 +52,21 @@ typedef struct sbt_handle sbt_handle;
 /* Detector geometry (section 1, Fig. 2: planes of pixel modules along z).
  * Module ids are given in traversal order: the reconstruction visits module
  * 0, 1, 2, ... (section "Track seeding and track following": the direction of
- * traversal is configurable, here by the order of module_z). */
+ * traversal is configurable, here by the order of module_z).
+ *
+ * Module pairs (the paper's method works on module pairs, the two sides of
+ * the VELO, and calls them modules; section "Search by triplet"): with
+ * module_z2 given, module i is a pair of one-sided planes, hits with x >= 0
+ * on the plane at module_z[i] and hits with x < 0 on the plane at
+ * module_z2[i].  Every extrapolation to a module then targets the plane of
+ * the hit it is compared with.  NULL module_z2: one plane per module.  The
+ * alignment adjoint (sbt_fit_adjoint) takes single planes only and returns
+ * SBT_ERR_ARG on a handle made with module_z2. */
 typedef struct {
     int32_t n_modules;      /* 3 .. 64 */
     const float* module_z;  /* host [n_modules]: plane z of module id i, mm; copied */
     float r_min, r_max;     /* active annulus, mm (informational) */
+    const float* module_z2; /* host [n_modules] or NULL: plane z of the x < 0 side of pair i; copied */
 } sbt_geometry;
 
 /* Tunable constants.  The paper states that the thresholds are configurable

@@ -314,6 +314,9 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
     std::memset(&h->C, 0, sizeof(h->C));
     h->C.M = geometry->n_modules;
     for (int m = 0; m < h->C.M; m++) h->C.module_z[m] = geometry->module_z[m];
+    h->C.pairs = geometry->module_z2 ? 1 : 0;
+    for (int m = 0; m < h->C.M; m++)
+        h->C.module_z2[m] = geometry->module_z2 ? geometry->module_z2[m] : geometry->module_z[m];
     h->C.K = c.k_doublets;
     h->C.S_seed = c.max_scatter_seed;
     h->C.S_follow = c.max_scatter_follow;
@@ -723,6 +726,7 @@ sbt_status sbt_fit_adjoint(sbt_handle* h, const float* x, const float* y, const 
                            double* chi2_sum, double* grad, void* stream)
 {
     if (!h) return SBT_ERR_ARG;
+    if (h->C.pairs) return fail(h, SBT_ERR_ARG, "the alignment adjoint takes single-plane modules");
     if (n_hits < 0 || n_tracks < 0) return fail(h, SBT_ERR_ARG, "negative size");
     if (!hit_offsets || !align || !chi2_sum || (n_tracks > 0 && (!track_hits || !x || !y || !z || !module)))
         return fail(h, SBT_ERR_ARG, "NULL argument");

@@ -22,6 +22,8 @@ struct DevConfig {
     int fcap;  // upper bound on forming tracks per event (0: forming_capacity(n) only)
     int gec;   // global event cut: events above this many hits are rejected (0: none)
     int h16;   // sorted hits stored as fp16 x, y, z + 16-bit index (8 bytes) instead of float4
+    int pairs; // module pairs: hits with x < 0 lie on the plane at module_z2 (0: single planes)
+    float module_z2[kMaxModules];
 };
 
 struct Inputs {

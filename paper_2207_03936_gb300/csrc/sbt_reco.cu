@@ -558,14 +558,36 @@ __device__ __forceinline__ bool window_of(float xp, float yp, float cut, float s
     return false;
 }
 
-// Visits the unflagged hits of module [b0, b0 + nb) inside the window that
-// starts at sorted index lo_idx (all hits when not windowed); the scatter of
-// every visited hit is computed exactly (rounded operations) and
-// `better(sc, b)` orders candidates under the cut.
-template <class Better, class Take, class HS>
+// Geometry of the module an extrapolation targets.  PlaneGeo: one plane at
+// module_z[m].  PairGeo: a module pair of one-sided planes (the paper's
+// method works on module pairs, the two sides of the VELO), hits with
+// x >= 0 on the plane at module_z[m] and hits with x < 0 on the plane at
+// module_z2[m]; a search visits each plane's hits with the prediction at
+// that plane's z, so every candidate is compared at its own plane.
+struct PlaneGeo {
+    static constexpr int kPlanes = 1;
+    __device__ __forceinline__ static float z(const DevConfig& C, int m, int) { return C.module_z[m]; }
+    __device__ __forceinline__ static bool on(int, float) { return true; }
+};
+
+struct PairGeo {
+    static constexpr int kPlanes = 2;
+    __device__ __forceinline__ static float z(const DevConfig& C, int m, int p)
+    {
+        return p ? C.module_z2[m] : C.module_z[m];
+    }
+    __device__ __forceinline__ static bool on(int p, float x) { return (x < 0.0f) == (p != 0); }
+};
+
+// Visits the unflagged hits of plane `plane` of module [b0, b0 + nb) inside
+// the window that starts at sorted index lo_idx (all hits when not
+// windowed); the scatter of every visited hit is computed exactly (rounded
+// operations) and `better(sc, b)` orders candidates under the cut.
+template <class G, class Better, class Take, class HS>
 __device__ __forceinline__ void scan_from(const Smem& S, const Region<HS>& R, int b0, int nb, float xp,
                                           float yp, float cut, bool windowed, int lo_idx,
-                                          uint32_t lo, uint32_t width, Better better, Take take)
+                                          uint32_t lo, uint32_t width, int plane, Better better,
+                                          Take take)
 {
     for (int k = 0; k < nb; k++) {
         int e = lo_idx + k;
@@ -573,21 +595,23 @@ __device__ __forceinline__ void scan_from(const Smem& S, const Region<HS>& R, in
         const int b = b0 + e;
         if (windowed && (((uint32_t)R.phi[b] - lo) & 0xFFFFu) > width) break;
         if (flagged(S, b)) continue;
-        const float sc = scatter_of(R.coords[b], xp, yp);
+        const float4 c = R.coords[b];
+        if (!G::on(plane, c.x)) continue;
+        const float sc = scatter_of(c, xp, yp);
         if (sc < cut && better(sc, b)) take(sc, b);
     }
 }
 
-template <class Better, class Take, class HS>
+template <class G, class Better, class Take, class HS>
 __device__ __forceinline__ void scan_window(const Smem& S, const Region<HS>& R, int b0, int nb, float xp,
-                                            float yp, float cut, float sqrt_cut, Better better,
-                                            Take take)
+                                            float yp, float cut, float sqrt_cut, int plane,
+                                            Better better, Take take)
 {
     if (nb <= 0) return;
     uint32_t lo, width;
     const bool windowed = window_of(xp, yp, cut, sqrt_cut, lo, width);
     const int lo_idx = windowed ? lower_bound16(R.phi + b0, nb, lo) : 0;
-    scan_from(S, R, b0, nb, xp, yp, cut, windowed, lo_idx, lo, width, better, take);
+    scan_from<G>(S, R, b0, nb, xp, yp, cut, windowed, lo_idx, lo, width, plane, better, take);
 }
 
 // First index in keys[0, n) whose upper 16 bits are >= v.
@@ -606,15 +630,18 @@ __device__ __forceinline__ int lower_bound_hi16(const uint32_t* keys, int n, uin
 
 constexpr int kSeedBatch = 1;
 
-// Candidates a[0, na) of one middle hit, processed together: extrapolations,
-// then the binary searches of their windows in lockstep (independent loads in
-// flight), then the window scans.  Keeps the best (scatter, a, b).
-template <class HS>
+// Candidates a[0, na) of one middle hit, processed together: extrapolations
+// to each plane of module i, then the binary searches of their windows in
+// lockstep (independent loads in flight), then the window scans.  Keeps the
+// best (scatter, a, b).
+template <class G, class HS>
 __device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& S, const Region<HS>& R,
-                                                int i0, int ni, float4 Cc, float zi, float sqrt_cut,
+                                                int i, int i0, int ni, float4 Cc, float sqrt_cut,
                                                 const int* a, int na, bool& have, float& best_sc,
                                                 int& best_a, int& best_b)
 {
+  for (int plane = 0; plane < G::kPlanes; plane++) {
+    const float zi = G::z(C, i, plane);
     float xp[kSeedBatch], yp[kSeedBatch];
     uint32_t lo[kSeedBatch], width[kSeedBatch];
     int L[kSeedBatch], H[kSeedBatch];
@@ -651,8 +678,8 @@ __device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& 
     for (int u = 0; u < kSeedBatch; u++) {
         if (u >= na) continue;
         const int au = a[u];
-        scan_from(
-            S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u],
+        scan_from<G>(
+            S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u], plane,
             [&](float sc, int b) {
                 return !have || sc < best_sc ||
                        (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
@@ -664,6 +691,7 @@ __device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& 
                 best_b = b;
             });
     }
+  }
 }
 
 // Seeding for middle hit c on module s+1: the unflagged hits of module s
@@ -673,7 +701,7 @@ __device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& 
 // (scatter, position of a, position of b).  `outer` lists the unflagged hits
 // of module s in sorted order as (phi16 << 16 | position), `nu` of them, so
 // the nearest-first walk visits no flagged hit.
-template <class HS>
+template <class G, class HS>
 __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R, int s, int c,
                          const uint32_t* outer, int nu, float sqrt_cut, int& oa, int& ob)
 {
@@ -681,7 +709,6 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
     if (nu <= 0 || ni <= 0) return false;
     const uint32_t phc = R.phi[c];
     const float4 Cc = R.coords[c];
-    const float zi = C.module_z[s + 2];
     const int j = lower_bound_hi16(outer, nu, phc);
     int up = j, dn = j - 1;
     int found = 0, dK = INT_MAX;
@@ -711,12 +738,12 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
         if (found == C.K) dK = d;
         cand[nc++] = a;
         if (nc == kSeedBatch) {
-            seed_candidates(C, S, R, i0, ni, Cc, zi, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
+            seed_candidates<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
             nc = 0;
         }
     }
     if (nc > 0)
-        seed_candidates(C, S, R, i0, ni, Cc, zi, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
+        seed_candidates<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
     if (have) {
         oa = best_a;
         ob = best_b;
@@ -725,24 +752,27 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
 }
 
 // Following: best unflagged hit on module t for the track's last two hits.
-template <class HS>
+template <class G, class HS>
 __device__ bool follow_best(const DevConfig& C, const Smem& S, const Region<HS>& R, int t, int h1, int h2,
                             float sqrt_cut, int& cand, float& csc)
 {
     const int b0 = S.modoff[t], nb = S.modoff[t + 1] - b0;
-    float xp, yp;
-    extrapolate(R.coords[h1], R.coords[h2], C.module_z[t], xp, yp);
+    const float4 A = R.coords[h1], Cc = R.coords[h2];
     bool have = false;
     float best = 0.0f;
     int bb = 0;
-    scan_window(
-        S, R, b0, nb, xp, yp, C.S_follow, sqrt_cut,
-        [&](float sc, int b) { return !have || sc < best || (sc == best && b < bb); },
-        [&](float sc, int b) {
-            have = true;
-            best = sc;
-            bb = b;
-        });
+    for (int plane = 0; plane < G::kPlanes; plane++) {
+        float xp, yp;
+        extrapolate(A, Cc, G::z(C, t, plane), xp, yp);
+        scan_window<G>(
+            S, R, b0, nb, xp, yp, C.S_follow, sqrt_cut, plane,
+            [&](float sc, int b) { return !have || sc < best || (sc == best && b < bb); },
+            [&](float sc, int b) {
+                have = true;
+                best = sc;
+                bb = b;
+            });
+    }
     cand = bb;
     csc = best;
     return have;
@@ -789,7 +819,7 @@ __device__ __forceinline__ FTrack make_track(int h0, int h1, int h2, int key, in
 // Following search of one forming track to module t and its claims: the new
 // hit, and for a 3-hit track also its three hits.  A 3-hit track with a
 // flagged hit cannot extend any more and is marked dead.
-template <class HS>
+template <class G, class HS>
 __device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem& S, const Region<HS>& R,
                                                  int t, unsigned long long tag, float sqrt_cut,
                                                  FTrack& T)
@@ -800,7 +830,7 @@ __device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem&
     }
     int b;
     float sc;
-    if (follow_best(C, S, R, t, T.h1, T.h2, sqrt_cut, b, sc)) {
+    if (follow_best<G>(C, S, R, t, T.h1, T.h2, sqrt_cut, b, sc)) {
         T.cand = (uint16_t)b;
         T.sc = sc;
         const unsigned long long k = claim_key(tag, sc, T.key);
@@ -827,7 +857,7 @@ __device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem&
 // Claims carry a tag (64 - t) << 48 above (scatter bits, track key), so a
 // claim of an earlier step always compares larger than one of the current
 // step and the claim words need no reset between steps.
-template <int NT, class HS>
+template <int NT, class G, class HS>
 __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem& S, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -898,17 +928,17 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
             if (i >= nl) {
                 if (follow) {
                     FTrack T = Fc[i - nl];
-                    follow_and_claim(C, S, R, t, tag, sq_follow, T);
+                    follow_and_claim<G>(C, S, R, t, tag, sq_follow, T);
                     Fc[i - nl] = T;
                 }
             } else {
                 const int c = (int)list[i];
                 int a, b;
-                if (seed_for(C, S, R, s, c, outer, nu, sq_seed, a, b)) {
+                if (seed_for<G>(C, S, R, s, c, outer, nu, sq_seed, a, b)) {
                     const int slot = nold + atomicAdd(&misc[kNew], 1);
                     if (slot < cap) {
                         FTrack T = make_track(a, c, b, c, 3, 0);
-                        if (follow) follow_and_claim(C, S, R, t, tag, sq_follow, T);
+                        if (follow) follow_and_claim<G>(C, S, R, t, tag, sq_follow, T);
                         Fc[slot] = T;
                     } else {
                         misc[kErr] = SBT_ERR_CAPACITY;
@@ -1132,7 +1162,7 @@ __device__ __forceinline__ void fail_event(int e, int code, const Staging& G, co
 }
 
 // Search of one sorted event by the whole block.
-template <int NT, class HS>
+template <int NT, class HS, class GEO>
 __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                           const Staging& G, const sbt_tracks& out, int e, int64_t hb, int64_t r,
                           int cap, const Smem& S)
@@ -1153,7 +1183,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
     // claim words of the modules that are never a following target
     for (int p = tid; p < S.modoff[min(3, C.M)]; p += NT) R.claim[p] = ~0ull;
     __syncthreads();
-    if (!search_stage<NT>(C, R, S, n)) {
+    if (!search_stage<NT, GEO>(C, R, S, n)) {
         fail_event(e, SBT_ERR_CAPACITY, G, out);
         __syncthreads();
         return;
@@ -1166,7 +1196,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
 // ------------------------------------------------------------- kernels ---
 
 // One block per event.
-template <int NT, class HS>
+template <int NT, class HS, class GEO>
 __global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sorted O, Work W,
                                                       Staging G, sbt_tracks out)
 {
@@ -1175,13 +1205,13 @@ __global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sor
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
-    run_event<NT, HS>(C, in, O, W, G, out, e, off, e, max(n, 0), S);
+    run_event<NT, HS, GEO>(C, in, O, W, G, out, e, off, e, max(n, 0), S);
 }
 
 // Persistent: each resident block takes events from the work queue, sizes
 // alternating from both ends of G.order (largest first), and reuses its own
 // scratch region.
-template <int NT, class HS>
+template <int NT, class HS, class GEO>
 __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in, Sorted O, Work W,
                                                            Staging G, sbt_tracks out)
 {
@@ -1201,7 +1231,7 @@ __global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in
         // order, are taken largest first, which keeps the tail short
         const int q0 = max(0, in.n_events - 2 * (int)gridDim.x) & ~1;
         const int qi = q >= q0 ? (q0 >> 1) + (q - q0) : (q & 1) ? in.n_events - 1 - (q >> 1) : (q >> 1);
-        run_event<NT, HS>(C, in, O, W, G, out, G.order[qi], hb, blockIdx.x, C.nmax, S);
+        run_event<NT, HS, GEO>(C, in, O, W, G, out, G.order[qi], hb, blockIdx.x, C.nmax, S);
     }
 }
 
@@ -1378,16 +1408,24 @@ cudaError_t launch_sort(const DevConfig& C, const Inputs& in, const Sorted& O, c
     return cudaGetLastError();
 }
 
+template <int NT, class HS, class GEO>
+static cudaError_t plain_ntg(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
+                             const Staging& G, const sbt_tracks& out, cudaStream_t st)
+{
+    size_t sm = smem_bytes(C.nmax, NT);
+    cudaError_t err = cudaFuncSetAttribute(k_search_plain<NT, HS, GEO>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (in.n_events > 0) k_search_plain<NT, HS, GEO><<<in.n_events, NT, sm, st>>>(C, in, O, W, G, out);
+    return cudaGetLastError();
+}
+
 template <int NT, class HS>
 static cudaError_t plain_nt(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                             const Staging& G, const sbt_tracks& out, cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_search_plain<NT, HS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    if (in.n_events > 0) k_search_plain<NT, HS><<<in.n_events, NT, sm, st>>>(C, in, O, W, G, out);
-    return cudaGetLastError();
+    return C.pairs ? plain_ntg<NT, HS, PairGeo>(C, in, O, W, G, out, st)
+                   : plain_ntg<NT, HS, PlaneGeo>(C, in, O, W, G, out, st);
 }
 
 cudaError_t launch_plain(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
@@ -1407,18 +1445,24 @@ cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream
     return cudaGetLastError();
 }
 
-template <int NT, class HS>
-static int occupancy_nt(const DevConfig& C)
+template <int NT, class HS, class GEO>
+static int occupancy_ntg(const DevConfig& C)
 {
     size_t sm = smem_bytes(C.nmax, NT);
-    if (cudaFuncSetAttribute(k_search_persistent<NT, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_search_persistent<NT, HS, GEO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_search_persistent<NT, HS>, NT, sm) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_search_persistent<NT, HS, GEO>, NT, sm) !=
         cudaSuccess)
         return 0;
     return blocks;
+}
+
+template <int NT, class HS>
+static int occupancy_nt(const DevConfig& C)
+{
+    return C.pairs ? occupancy_ntg<NT, HS, PairGeo>(C) : occupancy_ntg<NT, HS, PlaneGeo>(C);
 }
 
 int persistent_blocks_per_sm(const DevConfig& C, int threads)
@@ -1431,17 +1475,26 @@ int persistent_blocks_per_sm(const DevConfig& C, int threads)
     }
 }
 
+template <int NT, class HS, class GEO>
+static cudaError_t persistent_ntg(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
+                                  const Staging& G, const sbt_tracks& out, int blocks,
+                                  cudaStream_t st)
+{
+    size_t sm = smem_bytes(C.nmax, NT);
+    cudaError_t err = cudaFuncSetAttribute(k_search_persistent<NT, HS, GEO>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (blocks > 0) k_search_persistent<NT, HS, GEO><<<blocks, NT, sm, st>>>(C, in, O, W, G, out);
+    return cudaGetLastError();
+}
+
 template <int NT, class HS>
 static cudaError_t persistent_nt(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                                  const Staging& G, const sbt_tracks& out, int blocks,
                                  cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
-    cudaError_t err = cudaFuncSetAttribute(k_search_persistent<NT, HS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    if (blocks > 0) k_search_persistent<NT, HS><<<blocks, NT, sm, st>>>(C, in, O, W, G, out);
-    return cudaGetLastError();
+    return C.pairs ? persistent_ntg<NT, HS, PairGeo>(C, in, O, W, G, out, blocks, st)
+                   : persistent_ntg<NT, HS, PlaneGeo>(C, in, O, W, G, out, blocks, st);
 }
 
 cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,

@@ -417,12 +417,13 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
     S->max_batch = max_batch_events;
     cudaError_t e = cudaGetDevice(&S->device);
     const sbt::DevConfig& C = sbt::handle_device_config(h);
-    std::vector<float> mz(C.module_z, C.module_z + C.M);
+    std::vector<float> mz(C.module_z, C.module_z + C.M), mz2(C.module_z2, C.module_z2 + C.M);
     sbt_geometry g;
     g.n_modules = C.M;
     g.module_z = mz.data();
     g.r_min = 0.0f;
     g.r_max = 0.0f;
+    g.module_z2 = C.pairs ? mz2.data() : nullptr;
     sbt_config cfg;
     sbt_default_config(&cfg);
     cfg.k_doublets = C.K;

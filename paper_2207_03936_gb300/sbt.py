@@ -28,7 +28,8 @@ class SbtError(RuntimeError):
 
 class Geometry(ctypes.Structure):
     _fields_ = [("n_modules", ctypes.c_int32), ("module_z", ctypes.c_void_p),
-                ("r_min", ctypes.c_float), ("r_max", ctypes.c_float)]
+                ("r_min", ctypes.c_float), ("r_max", ctypes.c_float),
+                ("module_z2", ctypes.c_void_p)]
 
 
 class Config(ctypes.Structure):
@@ -179,10 +180,18 @@ class TrackOutput:
 class Handle:
     """Owns an sbt_handle (sbt_create / sbt_destroy)."""
 
-    def __init__(self, module_z, config: Config | None = None, r_min=5.1, r_max=42.0):
+    def __init__(self, module_z, config: Config | None = None, r_min=5.1, r_max=42.0,
+                 module_z2=None):
+        """module_z2: plane z of the x < 0 side of each module pair (None:
+        one plane per module)."""
         import numpy as np
         self._mz = np.ascontiguousarray(np.asarray(module_z, dtype=np.float32))
-        g = Geometry(self._mz.shape[0], self._mz.ctypes.data, r_min, r_max)
+        self._mz2 = (None if module_z2 is None
+                     else np.ascontiguousarray(np.asarray(module_z2, dtype=np.float32)))
+        if self._mz2 is not None and self._mz2.shape != self._mz.shape:
+            raise ValueError("module_z2 must have one entry per module")
+        g = Geometry(self._mz.shape[0], self._mz.ctypes.data, r_min, r_max,
+                     self._mz2.ctypes.data if self._mz2 is not None else None)
         h = ctypes.c_void_p()
         st = lib().sbt_create(ctypes.byref(g), ctypes.byref(config) if config is not None else None,
                               ctypes.byref(h))

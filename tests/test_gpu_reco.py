@@ -465,3 +465,45 @@ def test_maximum_event_size_bit_exact(sbt, fp16):
             assert g["track_offsets"][3] - g["track_offsets"][2] == ref.track_offsets[3] - ref.track_offsets[2]
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("config,n,fp16", [(2, 150, 0), (3, 60, 0), (2, 80, 1)])
+def test_module_pairs_bit_exact(sbt, config, n, fp16):
+    """Module-pair geometry (two one-sided planes per module, the x < 0 plane
+    at module_z2): plain, batched and host entry points equal the oracle's
+    pair reading, fp32 and fp16 storage."""
+    ev = synth.make_events(config, n, pairs=True)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(fp16_hits=fp16, **CFG), module_z2=ev.module_z2)
+    try:
+        o = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                               oracle.config(**CFG), fp16_hits=bool(fp16), module_z2=ev.module_z2)
+        assert o.n_tracks > 0
+        assert_same(run_gpu(sbt, h, ev, False), o)
+        assert_same(run_gpu(sbt, h, ev, True), o)
+        host = [torch.from_numpy(a) for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+        assert_same(sbt.sbt_reconstruct_host(h, *host).compact(), o)
+        # the same hits on a single-plane handle follow the single-plane reading
+        hs = sbt.sbt_create(ev.module_z, sbt.default_config(fp16_hits=fp16, **CFG))
+        try:
+            o1 = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, ev.module_z,
+                                    oracle.config(**CFG), fp16_hits=bool(fp16))
+            assert_same(run_gpu(sbt, hs, ev, True), o1)
+        finally:
+            hs.close()
+    finally:
+        h.close()
+
+
+def test_module_pairs_adjoint_is_refused(sbt):
+    ev = synth.make_events(2, 4, pairs=True, workers=1)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(**CFG), module_z2=ev.module_z2)
+    try:
+        dev = to_dev(ev)
+        out = sbt.sbt_reconstruct_batched(h, *dev).compact()
+        ho = torch.from_numpy(out["hit_offsets"]).cuda()
+        th = torch.from_numpy(out["track_hits"]).cuda()
+        align = torch.zeros(ev.module_z.shape[0], 6, dtype=torch.float64, device="cuda")
+        with pytest.raises(sbt.SbtError):
+            sbt.sbt_fit_adjoint(h, dev[0], dev[1], dev[2], dev[3], ho, th, align)
+    finally:
+        h.close()

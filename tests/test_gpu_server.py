@@ -138,3 +138,28 @@ def test_consecutive_schedules_reuse_the_pinned_batch():
             assert np.array_equal(r.hit_offsets, one.hit_offsets)
             assert np.array_equal(r.track_hits, one.track_hits)
             assert np.array_equal(r.params, one.params)
+
+
+def test_served_results_keep_module_pairs():
+    """Slots of a server made from a module-pair handle reconstruct with the
+    pair geometry: every served event equals the oracle's pair reading."""
+    from paper_2207_03936_gb300 import sbt
+    ev = synth.make_events(2, 60, seed=3, workers=1, pairs=True)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(), module_z2=ev.module_z2)
+    srv = sbt.Server(h, memory_budget_bytes=64 << 20, max_streams=2, max_batch_events=16)
+    try:
+        srv.submit_schedule(ev, np.zeros(ev.n_events))
+        got = collect(srv, ev.n_events)
+    finally:
+        srv.close()
+        h.close()
+    assert len(got) == ev.n_events
+    for e in range(ev.n_events):
+        lo, hi = ev.event_offsets[e], ev.event_offsets[e + 1]
+        one = oracle.event(ev.x[lo:hi], ev.y[lo:hi], ev.z[lo:hi], ev.module[lo:hi], ev.module_z,
+                           module_z2=ev.module_z2)
+        r = got[e]
+        assert r.status == 0
+        assert np.array_equal(r.hit_offsets, one.hit_offsets)
+        assert np.array_equal(r.track_hits, one.track_hits)
+        assert np.array_equal(r.params, one.params)
