@@ -640,58 +640,58 @@ __device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& 
                                                 const int* a, int na, bool& have, float& best_sc,
                                                 int& best_a, int& best_b)
 {
-  for (int plane = 0; plane < G::kPlanes; plane++) {
-    const float zi = G::z(C, i, plane);
-    float xp[kSeedBatch], yp[kSeedBatch];
-    uint32_t lo[kSeedBatch], width[kSeedBatch];
-    int L[kSeedBatch], H[kSeedBatch];
-    bool win[kSeedBatch];
-#pragma unroll
-    for (int u = 0; u < kSeedBatch; u++) {
-        L[u] = 0;
-        H[u] = 0;
-        win[u] = false;
-        if (u < na) {
-            extrapolate(R.coords[a[u]], Cc, zi, xp[u], yp[u]);
-            win[u] = window_of(xp[u], yp[u], C.S_seed, sqrt_cut, lo[u], width[u]);
-            H[u] = win[u] ? ni : 0;
-        }
-    }
-    const uint16_t* phi = R.phi + i0;
-    for (int it = 0; it < 17; it++) {
-        bool active = false;
-#pragma unroll
-        for (int u = 0; u < kSeedBatch; u++) active |= L[u] < H[u];
-        if (!active) break;
+    for (int plane = 0; plane < G::kPlanes; plane++) {
+        const float zi = G::z(C, i, plane);
+        float xp[kSeedBatch], yp[kSeedBatch];
+        uint32_t lo[kSeedBatch], width[kSeedBatch];
+        int L[kSeedBatch], H[kSeedBatch];
+        bool win[kSeedBatch];
 #pragma unroll
         for (int u = 0; u < kSeedBatch; u++) {
-            if (L[u] < H[u]) {
-                const int mid = (L[u] + H[u]) >> 1;
-                if ((uint32_t)phi[mid] < lo[u])
-                    L[u] = mid + 1;
-                else
-                    H[u] = mid;
+            L[u] = 0;
+            H[u] = 0;
+            win[u] = false;
+            if (u < na) {
+                extrapolate(R.coords[a[u]], Cc, zi, xp[u], yp[u]);
+                win[u] = window_of(xp[u], yp[u], C.S_seed, sqrt_cut, lo[u], width[u]);
+                H[u] = win[u] ? ni : 0;
             }
         }
-    }
+        const uint16_t* phi = R.phi + i0;
+        for (int it = 0; it < 17; it++) {
+            bool active = false;
 #pragma unroll
-    for (int u = 0; u < kSeedBatch; u++) {
-        if (u >= na) continue;
-        const int au = a[u];
-        scan_from<G>(
-            S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u], plane,
-            [&](float sc, int b) {
-                return !have || sc < best_sc ||
-                       (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
-            },
-            [&](float sc, int b) {
-                have = true;
-                best_sc = sc;
-                best_a = au;
-                best_b = b;
-            });
+            for (int u = 0; u < kSeedBatch; u++) active |= L[u] < H[u];
+            if (!active) break;
+#pragma unroll
+            for (int u = 0; u < kSeedBatch; u++) {
+                if (L[u] < H[u]) {
+                    const int mid = (L[u] + H[u]) >> 1;
+                    if ((uint32_t)phi[mid] < lo[u])
+                        L[u] = mid + 1;
+                    else
+                        H[u] = mid;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSeedBatch; u++) {
+            if (u >= na) continue;
+            const int au = a[u];
+            scan_from<G>(
+                S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u], plane,
+                [&](float sc, int b) {
+                    return !have || sc < best_sc ||
+                           (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
+                },
+                [&](float sc, int b) {
+                    have = true;
+                    best_sc = sc;
+                    best_a = au;
+                    best_b = b;
+                });
+        }
     }
-  }
 }
 
 // Seeding for middle hit c on module s+1: the unflagged hits of module s
