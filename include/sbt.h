@@ -64,7 +64,7 @@ typedef struct sbt_handle sbt_handle;
  * SBT_ERR_ARG on a handle made with module_z2. */
 typedef struct {
     int32_t n_modules;      /* 3 .. 64 */
-    const float* module_z;  /* host [n_modules]: plane z of module id i, mm; copied */
+    const float* module_z;  /* host [n_modules]: plane z of module id i, mm (finite); copied */
     float r_min, r_max;     /* active annulus, mm (informational) */
     const float* module_z2; /* host [n_modules] or NULL: plane z of the x < 0 side of pair i; copied */
 } sbt_geometry;
@@ -125,7 +125,10 @@ typedef struct {
 sbt_status sbt_default_config(sbt_config* out);
 
 /* Creates a handle: copies the geometry and configuration (cfg NULL = defaults).
- * Allocates only small device state; workspaces grow on first use. */
+ * Allocates only small device state; workspaces grow on first use.
+ * SBT_ERR_ARG (checked before any CUDA call; sbt_last_error(NULL) gives the
+ * reason): NULL geometry, module_z or out; n_modules outside [3, 64];
+ * a non-finite plane position; an invalid configuration value. */
 sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_handle** out);
 
 /* Waits for the handle's pending work and frees everything it owns. */

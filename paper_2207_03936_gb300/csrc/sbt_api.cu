@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -297,6 +298,12 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
         g_create_error = "n_modules must be in [3, 64]";
         return SBT_ERR_ARG;
     }
+    for (int m = 0; m < geometry->n_modules; m++)
+        if (!std::isfinite(geometry->module_z[m]) ||
+            (geometry->module_z2 && !std::isfinite(geometry->module_z2[m]))) {
+            g_create_error = "plane positions must be finite";
+            return SBT_ERR_ARG;
+        }
     sbt_config c;
     if (cfg)
         c = *cfg;
