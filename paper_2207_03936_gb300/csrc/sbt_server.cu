@@ -88,7 +88,10 @@ struct HostBuf {
 // Batches are pooled by the server: the last request that refers to one
 // returns it to the pool (freeing gigabytes of pinned memory takes tens of
 // milliseconds, which would hold up the results being published), and the
-// next schedule reuses it when it is large enough.
+// next schedule reuses it when it is large enough; at most kPinnedPool idle
+// batches are kept (the smallest go first).
+constexpr size_t kPinnedPool = 2;  // idle pinned batches a server keeps for reuse
+
 struct PinnedBatch {
     float *x = nullptr, *y = nullptr, *z = nullptr;
     int32_t* m = nullptr;
@@ -500,15 +503,24 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
     }
     const int32_t H = event_offsets[n_events];
     std::unique_ptr<PinnedBatch> pb;
+    std::vector<std::unique_ptr<PinnedBatch>> drop;  // idle batches beyond kPinnedPool, freed unlocked
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (auto it = S->pinned_pool.begin(); it != S->pinned_pool.end(); ++it)
+        auto& pool = S->pinned_pool;
+        for (auto it = pool.begin(); it != pool.end(); ++it)
             if ((*it)->cap >= (size_t)std::max(H, 1)) {
                 pb = std::move(*it);
-                S->pinned_pool.erase(it);
+                pool.erase(it);
                 break;
             }
+        while (pool.size() > kPinnedPool) {
+            auto smallest = std::min_element(pool.begin(), pool.end(),
+                                             [](const auto& a, const auto& b) { return a->cap < b->cap; });
+            drop.push_back(std::move(*smallest));
+            pool.erase(smallest);
+        }
     }
+    drop.clear();
     if (!pb) {
         pb.reset(new PinnedBatch());
         if (!pb->alloc((size_t)H)) return SBT_ERR_CUDA;
