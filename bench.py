@@ -285,17 +285,19 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     ev = synth.make_events(3, args.events)
-    per_step = []
+    per_step, step_ms = [], []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         res, _ = cpu_baseline(ev, args.cpu_seconds / max(args.steps, 1))
-        dt = time.perf_counter() - t0
         if s >= args.warmup:
             per_step.append(res["value"])
+            step_ms.append((time.perf_counter() - t0) * 1e3)
     v = float(np.mean(per_step))
     res["value"] = v
+    # a step is one bounded sample of the workload (cpu_baseline.sample says how large)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "events": ev.n_events, "hits": ev.n_hits},
             "cpu_baseline": res,
