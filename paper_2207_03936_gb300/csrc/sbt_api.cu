@@ -653,6 +653,14 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
         HH += Hc;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_out);
+    if (e != cudaSuccess) {
+        // nothing already queued may write into the caller's buffers after
+        // the call returns: let every stream of the pipeline drain first
+        cudaStreamSynchronize(h->copy_in);
+        cudaStreamSynchronize(h->sort_stream);
+        cudaStreamSynchronize(s);
+        cudaStreamSynchronize(h->copy_out);
+    }
     cleanup();
     if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline");
     if (E == 0) oh->track_offsets[0] = 0;
