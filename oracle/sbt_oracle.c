@@ -22,7 +22,7 @@
  *
  * Readings where the paper is silent (each one also applies to the CUDA path):
  *   R1 atan2: a degree-9 odd polynomial of the Hastings form tabulated in
- *      Abramowitz & Stegun 4.4.48, evaluated on the octant-reduced ratio,
+ *      Abramowitz & Stegun 4.4.49, evaluated on the octant-reduced ratio,
  *      every operation rounded in fp32 (its error against the exact atan on
  *      [0, 1] is at most 1.15e-5 rad, measured in fp64);
  *      phi16 = rint(a * 32768/pi) taken modulo 2^16.
@@ -81,7 +81,7 @@ typedef struct {
 /* ---------------------------------------------------------------- phi --- */
 
 /* R1: 2-argument arctangent from the odd polynomial atan(t) ~ t*(a1 + a3 t^2
- * + ... + a9 t^8), 0 <= t <= 1 (Hastings form, Abramowitz & Stegun 4.4.48),
+ * + ... + a9 t^8), 0 <= t <= 1 (Hastings form, Abramowitz & Stegun 4.4.49),
  * after reducing (x, y) to the first octant. */
 float sbt_oracle_atan2(float y, float x)
 {

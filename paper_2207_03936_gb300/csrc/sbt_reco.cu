@@ -38,7 +38,7 @@ constexpr uint16_t kDead = 0xFFFEu;
 // ------------------------------------------------------------------ phi ---
 
 // 2-argument arctangent: octant reduction and the degree-9 odd polynomial of
-// the Hastings form (Abramowitz & Stegun 4.4.48), every operation rounded.
+// the Hastings form (Abramowitz & Stegun 4.4.49), every operation rounded.
 __device__ __forceinline__ float atan2_sbt(float y, float x)
 {
     const float a1 = 0.9998660f, a3 = -0.3302995f, a5 = 0.1801410f;

@@ -10,7 +10,8 @@ import pytest
 
 import oracle
 from paper_2207_03936_gb300 import synth
-from tests.hand_events import MZ, assemble, line_hits, single_track
+from tests.hand_events import (MZ, assemble, following_tie, line_hits, seeding_tie, seeding_tie_third,
+                               single_track, tracklet_conflict)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -255,6 +256,11 @@ def test_hand_built_events(sbt, handle):
     cases.append((x, y, z, m))
     jit = np.where(np.arange(20) % 2 == 0, 0.003, -0.003)
     cases.append(line_hits(9.0, 0.0, 0.002, 0.0, range(5, 25), jitter=(np.zeros(20), jit)))
+    # ties and conflicts decided by the keys: overlapping tracklets (smaller
+    # chi2, then smaller key), following and seeding ties at bitwise-equal scatter
+    for build in (lambda: tracklet_conflict(False), lambda: tracklet_conflict(True), following_tie,
+                  seeding_tie, seeding_tie_third):
+        cases.append(build()[:4])
     xs, ys, zs, ms, offs = [], [], [], [], [0]
     for (x, y, z, m) in cases:
         xs.append(x); ys.append(y); zs.append(z); ms.append(m); offs.append(offs[-1] + len(x))
@@ -505,5 +511,29 @@ def test_module_pairs_adjoint_is_refused(sbt):
         align = torch.zeros(ev.module_z.shape[0], 6, dtype=torch.float64, device="cuda")
         with pytest.raises(sbt.SbtError):
             sbt.sbt_fit_adjoint(h, dev[0], dev[1], dev[2], dev[3], ho, th, align)
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("cfg_seed", range(4))
+def test_crowded_tiny_events_bit_exact(sbt, cfg_seed):
+    # the crowded tiny events of the oracle's whole-loop pin (overlapping
+    # seeds, contended extensions, overlapping tracklets), 200 per batch on
+    # eight planes, under four random configurations
+    from tests.test_oracle_loop import random_cfg, tiny_event
+    rng = np.random.default_rng(77 + cfg_seed)
+    module_z = (200.0 - 20.0 * np.arange(8)).astype(np.float32)
+    cfg = random_cfg(rng)
+    parts = [tiny_event(rng, module_z) for _ in range(200)]
+    offs = np.concatenate([[0], np.cumsum([len(p[0]) for p in parts])]).astype(np.int32)
+    ev = synth.Events(*(np.concatenate([p[k] for p in parts]) for k in range(3)),
+                      np.concatenate([p[3] for p in parts]).astype(np.int32), offs,
+                      np.zeros(offs[-1], np.int32), 0, module_z)
+    o = oracle.reconstruct(ev.x, ev.y, ev.z, ev.module, ev.event_offsets, module_z, oracle.config(**cfg))
+    assert o.n_tracks > 200
+    h = sbt.sbt_create(module_z, sbt.default_config(**cfg))
+    try:
+        for batched in (False, True):
+            assert_same(run_gpu(sbt, h, ev, batched), o)
     finally:
         h.close()

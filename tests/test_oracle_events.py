@@ -6,7 +6,8 @@ import numpy as np
 
 import oracle
 from paper_2207_03936_gb300 import synth
-from tests.hand_events import MZ, assemble, line_hits, single_track
+from tests.hand_events import (MZ, assemble, following_tie, line_hits, seeding_tie, seeding_tie_third,
+                               single_track, tracklet_conflict)
 
 
 def tracks_of(res):
@@ -122,3 +123,81 @@ def test_input_order_does_not_change_tracks():
         b = tracks_of(run(x[p], y[p], z[p], m[p]))
         b = {tuple(int(p[i]) for i in t) for t in b}
         assert a == b
+
+
+def test_overlapping_tracklets_smaller_chi2_survives():
+    # reading R7: both tracklets pass the cut with three unflagged hits; they
+    # share hit A, and the one with the smaller chi2 keeps it although its
+    # track key is the larger one
+    x, y, z, m, (t1, t2) = tracklet_conflict(equal_chi2=False)
+    q1 = float(oracle.fit(x[t1], y[t1], z[t1], 0.012)[1])
+    q2 = float(oracle.fit(x[t2], y[t2], z[t2], 0.012)[1])
+    assert q1 < q2 < 20.0
+    r = run(x, y, z, m)
+    assert tracks_of(r) == [t1]
+    assert int(r.stats[0, 1]) == 2 and int(r.stats[0, 2]) == 1   # two tracklets, one accepted
+    # with the cut between the two chi2 values only track 1 passes: same result
+    assert tracks_of(run(x, y, z, m, max_chi2_tracklet=(q1 + q2) / 2)) == [t1]
+    # with the cut below both neither survives
+    assert tracks_of(run(x, y, z, m, max_chi2_tracklet=q1 * 0.5)) == []
+
+
+def test_overlapping_tracklets_equal_chi2_go_to_smaller_track_key():
+    # the two tracklets are mirror images in y, so their chi2 are bitwise
+    # equal; the claim goes to the smaller track key, track 2 (its middle
+    # hit has the smaller phi16 and sorts first on module 31)
+    x, y, z, m, (t1, t2) = tracklet_conflict(equal_chi2=True)
+    q1 = oracle.fit(x[t1], y[t1], z[t1], 0.012)[1]
+    q2 = oracle.fit(x[t2], y[t2], z[t2], 0.012)[1]
+    assert q1.view(np.uint32) == q2.view(np.uint32)
+    perm, offs, _ = oracle.sort_event(x, y, m, 52)
+    pos = np.argsort(perm)
+    assert pos[t2[1]] < pos[t1[1]]
+    assert tracks_of(run(x, y, z, m)) == [t2]
+
+
+def _f32_scatter(ax, ay, az, cx, cy, cz, bx, by, zt):
+    f = np.float32
+    tz = f(f(f(zt) - f(cz)) / f(f(cz) - f(az)))
+    xp = f(f(cx) + f(f(f(cx) - f(ax)) * tz))
+    yp = f(f(cy) + f(f(f(cy) - f(ay)) * tz))
+    dx, dy = f(f(bx) - xp), f(f(by) - yp)
+    return f(f(dx * dx) + f(dy * dy))
+
+
+def test_following_tie_goes_to_smaller_sorted_position():
+    # reading R5: two hits on module 15 at bitwise-equal scatter from the
+    # track's prediction; the one with the smaller sorted position is taken
+    x, y, z, m, track = following_tie()
+    k = [i for i in range(len(x)) if m[i] == 15]
+    assert len(k) == 2
+    prev = [i for i in track if m[i] in (13, 14)]
+    s = [_f32_scatter(x[prev[0]], y[prev[0]], z[prev[0]], x[prev[1]], y[prev[1]], z[prev[1]],
+                      x[i], y[i], MZ[15]) for i in k]
+    assert s[0].view(np.uint32) == s[1].view(np.uint32) and s[0] < 0.04
+    assert tracks_of(run(x, y, z, m)) == [track]
+
+
+def test_seeding_tie_goes_to_smaller_outer_position():
+    # reading R4: the triplets (A1, C, B1) and (A2, C, B2) have bitwise-equal
+    # scatter; the kept one has the outer hit of smaller sorted position
+    x, y, z, m, tl = seeding_tie()
+    a1, c, b1 = tl
+    a2 = [i for i in range(len(x)) if m[i] == 30 and i != a1][0]
+    b2 = [i for i in range(len(x)) if m[i] == 32 and i != b1][0]
+    s1 = _f32_scatter(x[a1], y[a1], z[a1], x[c], y[c], z[c], x[b1], y[b1], MZ[32])
+    s2 = _f32_scatter(x[a2], y[a2], z[a2], x[c], y[c], z[c], x[b2], y[b2], MZ[32])
+    assert s1.view(np.uint32) == s2.view(np.uint32) and s1 < 0.04
+    assert tracks_of(run(x, y, z, m)) == [tl]
+
+
+def test_seeding_tie_goes_to_smaller_third_position():
+    # reading R4: one doublet, two third hits at bitwise-equal scatter; the
+    # kept one has the smaller sorted position
+    x, y, z, m, tl = seeding_tie_third()
+    a, c, b1 = tl
+    b2 = [i for i in range(len(x)) if m[i] == 32 and i != b1][0]
+    s1 = _f32_scatter(x[a], y[a], z[a], x[c], y[c], z[c], x[b1], y[b1], MZ[32])
+    s2 = _f32_scatter(x[a], y[a], z[a], x[c], y[c], z[c], x[b2], y[b2], MZ[32])
+    assert s1.view(np.uint32) == s2.view(np.uint32) and s1 < 0.04
+    assert tracks_of(run(x, y, z, m)) == [tl]

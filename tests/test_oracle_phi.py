@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 
-# The degree-9 polynomial (Hastings form, Abramowitz & Stegun 4.4.48) with the
+# The degree-9 polynomial (Hastings form, Abramowitz & Stegun 4.4.49) with the
 # coefficients of the reading R1 deviates from atan on [0, 1] by at most
 # 1.15e-5 rad in exact arithmetic (test_polynomial_error_in_fp64); the fp32
 # evaluation and octant reconstruction add at most a few ulp of pi.
