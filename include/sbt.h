@@ -99,7 +99,9 @@ typedef struct {
  *   params        [cap_tracks * 4] x0, y0, tx, ty of x = x0 + tx z, y = y0 + ty z
  *   chi2          [cap_tracks]     sum of squared residuals / hit_sigma^2
  *   ndof          [cap_tracks]     2 * hits - 4
- *   event_status  [n_events]       SBT_OK, SBT_ERR_ARG (module id out of range),
+ *   event_status  [n_events]       SBT_OK, SBT_ERR_ARG (module id out of range, or
+ *                                  hit range [event_offsets[e], event_offsets[e+1])
+ *                                  not inside [0, n_hits)),
  *                                  SBT_ERR_CAPACITY (event above max_hits_per_event
  *                                  or a per-event buffer full) or SBT_EVENT_CUT (above
  *                                  gec_max_hits); failed and cut events have no tracks
@@ -144,6 +146,10 @@ const char* sbt_last_error(const sbt_handle* h);
  * Table 1).  Inputs (device): x, y, z [n_hits] fp32 mm, module [n_hits]
  * traversal-order module id, event_offsets [n_events + 1] (event e owns hits
  * [event_offsets[e], event_offsets[e+1])), n_hits = event_offsets[n_events].
+ * The library reads event_offsets only on the device: an event whose hit
+ * range is not inside [0, n_hits) gets event status SBT_ERR_ARG and nothing
+ * of it is read or written beyond its offsets; x, y, z and module are read
+ * at [0, n_hits) only.
  * Outputs: *out (device arrays described at sbt_tracks).
  */
 sbt_status sbt_reconstruct(sbt_handle* h, const float* x, const float* y, const float* z,
@@ -169,7 +175,9 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
  * memory; counts is host too).  The batch is processed in chunks of whole
  * events so that uploads, kernels and downloads of different chunks overlap.
  * Synchronous: returns when the host arrays are filled.  Pinned host memory
- * gives full copy bandwidth and true overlap.
+ * gives full copy bandwidth and true overlap.  event_offsets (host here) must
+ * be non-decreasing from event_offsets[0] >= 0 to event_offsets[n_events] <=
+ * n_hits, else SBT_ERR_ARG and nothing is enqueued.
  */
 sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, const float* z,
                                 const int32_t* module, const int32_t* event_offsets,
@@ -188,21 +196,31 @@ sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const flo
 
 /*
  * Differentiation of the consolidation fit with respect to per-module
- * alignment.  For a hit h on module m with plane centre c = (0, 0, module_z[m])
- * and align[6m .. 6m+5] = (dx, dy, dz, a, b, g) (mm, rad), the aligned hit is
+ * alignment (the fit is the least-squares line of the paper's tracklet
+ * filter and data consolidation, section "Search by triplet"; the alignment
+ * objective itself has no counterpart in the paper).  For a hit h on module
+ * m with plane centre c = (0, 0, module_z[m]) and align[6m .. 6m+5] =
+ * (dx, dy, dz, a, b, g) (mm, rad), the aligned hit is
  *     h' = Rz(g) Ry(b) Rx(a) (h - c) + c + (dx, dy, dz).
  * Every track (hit lists fixed, e.g. the output of sbt_reconstruct) is refitted
  * by least squares on its aligned hits, in fp64; *chi2_sum = sum over tracks of
  * the squared residuals / hit_sigma^2, grad = d chi2_sum / d align [n_modules*6],
  * accumulated in fp64 in a fixed order (bitwise reproducible).
+ * A track may have any number of hits, several on one module included.  A
+ * track contributes nothing, and is counted in *skipped, when it has no
+ * straight-line fit (fewer than two hits, or all its hits on one module), when
+ * one of its hit indices is outside [0, n_hits) or the module id of one of its
+ * hits outside [0, n_modules), or when its range of track_hits is not inside
+ * [0, hit_offsets[n_tracks]).
  * Inputs (device): x, y, z, module [n_hits]; hit_offsets [n_tracks + 1];
- * track_hits; align [n_modules * 6] fp64.  Outputs (device): chi2_sum [1],
- * grad [n_modules * 6] fp64 (grad may be NULL for the value alone).
+ * track_hits [hit_offsets[n_tracks]]; align [n_modules * 6] fp64.  Outputs
+ * (device): chi2_sum [1], grad [n_modules * 6] fp64 (NULL for the value
+ * alone), skipped [1] int32 (may be NULL).
  */
 sbt_status sbt_fit_adjoint(sbt_handle* h, const float* x, const float* y, const float* z,
                            const int32_t* module, int32_t n_hits, const int32_t* hit_offsets,
                            const int32_t* track_hits, int32_t n_tracks, const double* align,
-                           double* chi2_sum, double* grad, void* stream);
+                           double* chi2_sum, double* grad, int32_t* skipped, void* stream);
 
 /*
  * Stage output of the phi sort (section "Sort by phi"), for checking it in
@@ -237,12 +255,14 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
  * application that owns the device memory pool.  The paper has no
  * counterpart; it computes exactly what sbt_reconstruct computes.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *     workspace is a fixed array of about 40 MB inside the library's device
+ *     workspace is a fixed array of about 45 MB inside the library's device
  *     image, held by every GPU that loads the library until the process exits.
  *   - At most 524288 hits and 4096 events per call; larger batches return
  *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).
  *   - The first call on each device looks up the workspace address on that
- *     device; make that first call before any stream capture.
+ *     device; make that first call before any stream capture.  The address
+ *     is kept until the process exits: do not call this entry point on a
+ *     device after cudaDeviceReset on it (the reset unloads the workspace).
  *   - Every call on a device shares the one workspace: calls whose work
  *     overlaps on the GPU (other streams, other handles, other threads) race
  *     and corrupt each other's results; serialise them.
@@ -300,7 +320,9 @@ sbt_status sbt_server_submit(sbt_server* s, int64_t request_id, const float* x, 
  * from that scheduled time.  The call copies the
  * batch into pinned host memory (uploads of consecutive events then need no
  * further copy) and returns at once; results arrive through
- * sbt_server_poll or sbt_server_drain. */
+ * sbt_server_poll or sbt_server_drain.  event_offsets must be non-decreasing
+ * from event_offsets[0] >= 0 (else SBT_ERR_ARG); the hit arrays hold at least
+ * event_offsets[n_events] entries. */
 sbt_status sbt_server_submit_schedule(sbt_server* s, const float* x, const float* y,
                                       const float* z, const int32_t* module,
                                       const int32_t* event_offsets, int32_t n_events,

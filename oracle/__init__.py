@@ -95,9 +95,9 @@ def lib() -> ctypes.CDLL:
                                            ctypes.c_int32,
                                            ctypes.c_void_p, _i32p, _i32p, _i32p]
         L.sbt_oracle_align_chi2.restype = ctypes.c_double
-        L.sbt_oracle_align_chi2.argtypes = [_f32p, _f32p, _f32p, _i32p, _i32p, _i32p,
+        L.sbt_oracle_align_chi2.argtypes = [_f32p, _f32p, _f32p, _i32p, ctypes.c_int32, _i32p, _i32p,
                                             ctypes.c_int32, _f32p, ctypes.c_int32, _f64p,
-                                            ctypes.c_double, ctypes.c_void_p]
+                                            ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -274,13 +274,19 @@ def seed_step(x, y, z, module, module_z, s: int, cfg: Config | None = None, flag
 
 
 def align_chi2(x, y, z, module, hit_offsets, track_hits, module_z, align, sigma: float,
-               want_grad: bool = True):
-    """fp64 summed chi2 of fixed tracks after per-module alignment, and its gradient."""
+               want_grad: bool = True, count_skipped: bool = False):
+    """fp64 summed chi2 of fixed tracks after per-module alignment, and its
+    gradient; with count_skipped also the number of tracks without a
+    straight-line fit (fewer than two hits or modules, or an index out of
+    range), which contribute nothing."""
     x, y, z, module = _f32(x), _f32(y), _f32(z), _i32(module)
     ho, th, module_z = _i32(hit_offsets), _i32(track_hits), _f32(module_z)
     align = np.ascontiguousarray(align, dtype=np.float64).reshape(-1)
     M = module_z.shape[0]
     g = np.zeros(6 * M, np.float64) if want_grad else None
-    v = lib().sbt_oracle_align_chi2(x, y, z, module, ho, th, ho.shape[0] - 1, module_z, M, align,
-                                    float(sigma), g.ctypes.data if g is not None else None)
-    return v, (g.reshape(M, 6) if g is not None else None)
+    sk = np.zeros(1, np.int32)
+    v = lib().sbt_oracle_align_chi2(x, y, z, module, x.shape[0], ho, th, ho.shape[0] - 1, module_z, M,
+                                    align, float(sigma), g.ctypes.data if g is not None else None,
+                                    sk.ctypes.data)
+    res = (v, (g.reshape(M, 6) if g is not None else None))
+    return res + (int(sk[0]),) if count_skipped else res

@@ -759,21 +759,53 @@ int32_t sbt_oracle_batch(const float* x, const float* y, const float* z, const i
  * is not NULL it receives d(chi2 sum)/d(align) [M * 6], using that at the
  * least-squares optimum the derivative with respect to each hit is the
  * partial derivative at fixed line parameters.
+ *
+ * A track takes part when it has a straight-line fit: at least two hits,
+ * hits on at least two modules, every hit index in [0, n_hits), every module
+ * id in [0, M), and its hit range inside [0, hit_offsets[n_tracks]).  Other
+ * tracks contribute nothing; *skipped (may be NULL) receives their number.
+ * A track may have any number of hits, several on one module included.
  */
 double sbt_oracle_align_chi2(const float* x, const float* y, const float* z, const int32_t* module,
-                             const int32_t* hit_offsets, const int32_t* track_hits,
+                             int32_t n_hits, const int32_t* hit_offsets, const int32_t* track_hits,
                              int32_t n_tracks, const float* module_z, int32_t M,
-                             const double* align, double sigma, double* grad)
+                             const double* align, double sigma, double* grad, int32_t* skipped)
 {
     double total = 0.0;
+    int32_t nskip = 0;
     if (grad)
         for (int32_t k = 0; k < 6 * M; k++) grad[k] = 0.0;
     double s2 = sigma * sigma;
+    const int64_t end = n_tracks > 0 ? hit_offsets[n_tracks] : 0;
+    int32_t cap = 0;
+    double *px = NULL, *py = NULL, *pz = NULL, *lx = NULL, *ly = NULL, *lz = NULL;
+    int32_t* mod = NULL;
     for (int32_t t = 0; t < n_tracks; t++) {
         int32_t h0 = hit_offsets[t], n = hit_offsets[t + 1] - hit_offsets[t];
-        double px[OR_MAX_MODULES], py[OR_MAX_MODULES], pz[OR_MAX_MODULES];
-        double lx[OR_MAX_MODULES], ly[OR_MAX_MODULES], lz[OR_MAX_MODULES];
-        int32_t mod[OR_MAX_MODULES];
+        int ok = n >= 2 && h0 >= 0 && (int64_t)h0 + n <= end;
+        for (int32_t j = 0; ok && j < n; j++) {
+            int32_t h = track_hits[h0 + j];
+            ok = h >= 0 && h < n_hits && module[h] >= 0 && module[h] < M;
+        }
+        if (ok) {
+            int two = 0;
+            for (int32_t j = 1; j < n; j++) two = two || module[track_hits[h0 + j]] != module[track_hits[h0]];
+            ok = two;
+        }
+        if (!ok) {
+            nskip++;
+            continue;
+        }
+        if (n > cap) {
+            cap = n;
+            px = (double*)realloc(px, sizeof(double) * (size_t)cap);
+            py = (double*)realloc(py, sizeof(double) * (size_t)cap);
+            pz = (double*)realloc(pz, sizeof(double) * (size_t)cap);
+            lx = (double*)realloc(lx, sizeof(double) * (size_t)cap);
+            ly = (double*)realloc(ly, sizeof(double) * (size_t)cap);
+            lz = (double*)realloc(lz, sizeof(double) * (size_t)cap);
+            mod = (int32_t*)realloc(mod, sizeof(int32_t) * (size_t)cap);
+        }
         for (int32_t j = 0; j < n; j++) {
             int32_t h = track_hits[h0 + j];
             int32_t m = module[h];
@@ -845,5 +877,13 @@ double sbt_oracle_align_chi2(const float* x, const float* y, const float* z, con
             }
         }
     }
+    free(px);
+    free(py);
+    free(pz);
+    free(lx);
+    free(ly);
+    free(lz);
+    free(mod);
+    if (skipped) *skipped = nskip;
     return total;
 }

@@ -9,11 +9,14 @@
 //     d chi2 / d h' = 2 / sigma^2 (rx, ry, -(rx tx + ry ty)),
 // chained through d h' / d(align_m).
 //
-// Layout: one warp per track, lanes over its hits (a track has at most one
-// hit per module, so the lanes of a warp update distinct modules).  Each warp
-// owns an fp64 accumulator in shared memory; warps are summed in a fixed
-// order per block and blocks in a fixed order by the final kernel, so the
-// result is bitwise reproducible.  Arithmetic is fp64 (the hits are fp32).
+// Layout: one warp per track, lanes over its hits in rounds of 32.  A track
+// may have any number of hits and several hits on one module; a track
+// without a straight-line fit (fewer than two hits or modules) or with an
+// index out of range contributes nothing and is counted as skipped.  Each
+// warp owns an fp64 accumulator in shared memory, updated in a fixed lane
+// order; warps are summed in a fixed order per block and blocks in a fixed
+// order by the final kernel, so the result is bitwise reproducible.
+// Arithmetic is fp64 (the hits are fp32).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -24,9 +27,9 @@ namespace sbt {
 
 constexpr int kAdjThreads = 256;
 constexpr int kAdjWarps = kAdjThreads / 32;
-constexpr int kAdjBlocks = 152 * 4;
+constexpr int kAdjBlocksPerSM = 4;
 
-int adjoint_blocks() { return kAdjBlocks; }
+int adjoint_blocks(int sm_count) { return kAdjBlocksPerSM * (sm_count > 0 ? sm_count : 1); }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -74,6 +77,32 @@ __device__ void module_matrices(const double* th, double* out /* 36 */)
     (void)t2;
 }
 
+// One aligned hit: its module, the local coordinates v = h - c_m and the
+// aligned position p = R_m v + c_m + t_m.
+struct AHit {
+    double px, py, pz, vx, vy, vz;
+    int m;
+};
+
+__device__ __forceinline__ AHit aligned_hit(const DevConfig& C, const Inputs& in, const double* mats,
+                                            const double* align, int h)
+{
+    AHit a;
+    a.m = in.module[h];
+    const double* R = mats + 36 * a.m;
+    const double* th = align + 6 * a.m;
+    const double zc = (double)C.module_z[a.m];
+    a.vx = (double)in.x[h];
+    a.vy = (double)in.y[h];
+    a.vz = (double)in.z[h] - zc;
+    double ox, oy, oz;
+    matvec(R, a.vx, a.vy, a.vz, ox, oy, oz);
+    a.px = ox + th[0];
+    a.py = oy + th[1];
+    a.pz = oz + zc + th[2];
+    return a;
+}
+
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
                                                           const int32_t* hit_offsets,
                                                           const int32_t* track_hits,
@@ -82,7 +111,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = C.M;
-    const int P = 6 * M + 1;  // gradient entries + chi2
+    const int P = 6 * M + 2;  // gradient entries, chi2, skipped tracks
     double* mats = (double*)smem_raw;               // [M][36]
     double* acc = mats + 36 * M;                    // [warps][P]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -93,73 +122,119 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
     const double s2 = (double)C.sigma * (double)C.sigma;
     const int gw = blockIdx.x * kAdjWarps + warp;
     const int nw = gridDim.x * kAdjWarps;
+    const int64_t end = n_tracks > 0 ? hit_offsets[n_tracks] : 0;
     for (int t = gw; t < n_tracks; t += nw) {
         const int h0 = hit_offsets[t];
         const int n = hit_offsets[t + 1] - h0;
-        // each lane holds up to two hits (tracks have at most 64 hits)
-        double px[2] = {0, 0}, py[2] = {0, 0}, pz[2] = {0, 0};
-        double vx[2] = {0, 0}, vy[2] = {0, 0}, vz[2] = {0, 0};
-        int mod[2] = {-1, -1};
-        double sx = 0, sy = 0, sz = 0;
-        for (int r = 0; r < 2; r++) {
-            int j = lane + 32 * r;
-            if (j >= n) continue;
-            int h = track_hits[h0 + j];
-            int m = in.module[h];
-            const double* R = mats + 36 * m;
-            const double* th = align + 6 * m;
-            double zc = (double)C.module_z[m];
-            double lx = (double)in.x[h], ly = (double)in.y[h], lz = (double)in.z[h] - zc;
-            double ox, oy, oz;
-            matvec(R, lx, ly, lz, ox, oy, oz);
-            px[r] = ox + th[0];
-            py[r] = oy + th[1];
-            pz[r] = oz + zc + th[2];
-            vx[r] = lx;
-            vy[r] = ly;
-            vz[r] = lz;
-            mod[r] = m;
-            sx += px[r];
-            sy += py[r];
-            sz += pz[r];
+        // every lane reads the same offsets, so these branches are uniform
+        if (n < 2 || h0 < 0 || (int64_t)h0 + n > end) {
+            if (lane == 0) my[6 * M + 1] += 1.0;
+            continue;
         }
+        // pass 1: validity, sums; hits 0..63 kept in registers (two per lane)
+        AHit keep0, keep1;
+        bool bad = false;
+        int mlo = INT32_MAX, mhi = -1;
+        double sx = 0, sy = 0, sz = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int j = base + lane;
+            if (j >= n) continue;
+            const int h = track_hits[h0 + j];
+            if (h < 0 || h >= in.n_hits || in.module[h] < 0 || in.module[h] >= M) {
+                bad = true;
+                continue;
+            }
+            const AHit a = aligned_hit(C, in, mats, align, h);
+            if (base == 0)
+                keep0 = a;
+            else if (base == 32)
+                keep1 = a;
+            mlo = min(mlo, a.m);
+            mhi = max(mhi, a.m);
+            sx += a.px;
+            sy += a.py;
+            sz += a.pz;
+        }
+        bad = __any_sync(0xFFFFFFFFu, bad);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mlo = min(mlo, __shfl_xor_sync(0xFFFFFFFFu, mlo, o));
+            mhi = max(mhi, __shfl_xor_sync(0xFFFFFFFFu, mhi, o));
+        }
+        if (bad || mlo == mhi) {
+            if (lane == 0) my[6 * M + 1] += 1.0;
+            continue;
+        }
+        auto hit_at = [&](int base, int j) -> AHit {
+            if (base == 0) return keep0;
+            if (base == 32) return keep1;
+            return aligned_hit(C, in, mats, align, track_hits[h0 + j]);
+        };
         sx = warp_sum(sx);
         sy = warp_sum(sy);
         sz = warp_sum(sz);
         const double xm = sx / n, ym = sy / n, zm = sz / n;
+        // pass 2: second moments
         double szz = 0, szx = 0, szy = 0;
-        for (int r = 0; r < 2; r++) {
-            if (mod[r] < 0) continue;
-            double dz = pz[r] - zm;
+        for (int base = 0; base < n; base += 32) {
+            const int j = base + lane;
+            if (j >= n) continue;
+            const AHit a = hit_at(base, j);
+            const double dz = a.pz - zm;
             szz += dz * dz;
-            szx += dz * (px[r] - xm);
-            szy += dz * (py[r] - ym);
+            szx += dz * (a.px - xm);
+            szy += dz * (a.py - ym);
         }
         szz = warp_sum(szz);
         szx = warp_sum(szx);
         szy = warp_sum(szy);
         const double tx = szx / szz, ty = szy / szz;
+        // pass 3: residuals, chi2 and the gradient per module; lanes of one
+        // round that share a module add in lane order
         double c2 = 0;
-        for (int r = 0; r < 2; r++) {
-            if (mod[r] < 0) continue;
-            double dz = pz[r] - zm;
-            double rx = (px[r] - xm) - tx * dz;
-            double ry = (py[r] - ym) - ty * dz;
-            c2 += (rx * rx + ry * ry) / s2;
-            if (!want_grad) continue;
-            double gx = 2.0 * rx / s2, gy = 2.0 * ry / s2, gz = -(2.0 * rx * tx + 2.0 * ry * ty) / s2;
-            const double* D = mats + 36 * mod[r];
-            double ux, uy, uz;
-            double* G = my + 6 * mod[r];
-            G[0] += gx;
-            G[1] += gy;
-            G[2] += gz;
-            matvec(D + 9, vx[r], vy[r], vz[r], ux, uy, uz);
-            G[3] += gx * ux + gy * uy + gz * uz;
-            matvec(D + 18, vx[r], vy[r], vz[r], ux, uy, uz);
-            G[4] += gx * ux + gy * uy + gz * uz;
-            matvec(D + 27, vx[r], vy[r], vz[r], ux, uy, uz);
-            G[5] += gx * ux + gy * uy + gz * uz;
+        for (int base = 0; base < n; base += 32) {
+            const int j = base + lane;
+            const bool act = j < n;
+            double g[6] = {0, 0, 0, 0, 0, 0};
+            int m = -1 - lane;  // distinct for inactive lanes
+            if (act) {
+                const AHit a = hit_at(base, j);
+                m = a.m;
+                const double dz = a.pz - zm;
+                const double rx = (a.px - xm) - tx * dz;
+                const double ry = (a.py - ym) - ty * dz;
+                c2 += (rx * rx + ry * ry) / s2;
+                const double gx = 2.0 * rx / s2, gy = 2.0 * ry / s2, gz = -(2.0 * rx * tx + 2.0 * ry * ty) / s2;
+                const double* D = mats + 36 * m;
+                double ux, uy, uz;
+                g[0] = gx;
+                g[1] = gy;
+                g[2] = gz;
+                matvec(D + 9, a.vx, a.vy, a.vz, ux, uy, uz);
+                g[3] = gx * ux + gy * uy + gz * uz;
+                matvec(D + 18, a.vx, a.vy, a.vz, ux, uy, uz);
+                g[4] = gx * ux + gy * uy + gz * uz;
+                matvec(D + 27, a.vx, a.vy, a.vz, ux, uy, uz);
+                g[5] = gx * ux + gy * uy + gz * uz;
+            }
+            if (want_grad) {
+                const unsigned same = __match_any_sync(0xFFFFFFFFu, m);
+                if (!__any_sync(0xFFFFFFFFu, __popc(same) > 1)) {
+                    if (act) {
+#pragma unroll
+                        for (int k = 0; k < 6; k++) my[6 * m + k] += g[k];
+                    }
+                } else {
+                    for (int l = 0; l < 32; l++) {
+                        if (lane == l && act) {
+#pragma unroll
+                            for (int k = 0; k < 6; k++) my[6 * m + k] += g[k];
+                        }
+                        __syncwarp();
+                    }
+                }
+                __syncwarp();
+            }
         }
         c2 = warp_sum(c2);
         if (lane == 0) my[6 * M] += c2;
@@ -174,33 +249,37 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
 }
 
 __global__ void k_adjoint_reduce(int M, int blocks, const double* partial, double* chi2_sum,
-                                 double* grad)
+                                 double* grad, int32_t* skipped)
 {
-    const int P = 6 * M + 1;
+    const int P = 6 * M + 2;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
         double s = 0;
         for (int b = 0; b < blocks; b++) s += partial[(int64_t)b * P + k];
         if (k < 6 * M) {
             if (grad) grad[k] = s;
-        } else {
+        } else if (k == 6 * M) {
             *chi2_sum = s;
+        } else if (skipped) {
+            *skipped = (int32_t)s;
         }
     }
 }
 
+size_t adjoint_partial_entries(int M, int blocks) { return (size_t)blocks * (6 * (size_t)M + 2); }
+
 cudaError_t launch_adjoint(const DevConfig& C, const Inputs& in, const int32_t* hit_offsets,
                            const int32_t* track_hits, int32_t n_tracks, const double* align,
-                           double* chi2_sum, double* grad, const AdjointWork& W,
+                           double* chi2_sum, double* grad, int32_t* skipped, const AdjointWork& W,
                            cudaStream_t stream)
 {
     const int M = C.M;
-    size_t sm = sizeof(double) * (36 * (size_t)M + (size_t)kAdjWarps * (6 * M + 1));
+    size_t sm = sizeof(double) * (36 * (size_t)M + (size_t)kAdjWarps * (6 * M + 2));
     cudaError_t err = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sm);
     if (err != cudaSuccess) return err;
     k_adjoint<<<W.blocks, kAdjThreads, sm, stream>>>(C, in, hit_offsets, track_hits, n_tracks,
                                                       align, W.partial, grad != nullptr);
-    k_adjoint_reduce<<<2, 256, 0, stream>>>(M, W.blocks, W.partial, chi2_sum, grad);
+    k_adjoint_reduce<<<2, 256, 0, stream>>>(M, W.blocks, W.partial, chi2_sum, grad, skipped);
     return cudaGetLastError();
 }
 

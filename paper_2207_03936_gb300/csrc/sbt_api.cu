@@ -194,6 +194,15 @@ sbt_status check_inputs(sbt_handle* h, const float* x, const float* y, const flo
     return SBT_OK;
 }
 
+// Host-visible event offsets: non-decreasing, from 0 or more up to n_hits.
+bool host_offsets_valid(const int32_t* offsets, int32_t n_events, int64_t n_hits)
+{
+    if (offsets[0] < 0 || offsets[n_events] > n_hits) return false;
+    for (int32_t e = 0; e < n_events; e++)
+        if (offsets[e] > offsets[e + 1]) return false;
+    return true;
+}
+
 Inputs make_inputs(const float* x, const float* y, const float* z, const int32_t* module,
                    const int32_t* offsets, int32_t n_events, int32_t n_hits)
 {
@@ -266,6 +275,8 @@ const DevConfig& handle_device_config(const sbt_handle* h) { return h->C; }
 int handle_plain_threads(const sbt_handle* h) { return default_threads(h, false); }
 
 void handle_set_error(sbt_handle* h, const std::string& msg) { h->err = msg; }
+
+void handle_set_launches(sbt_handle* h, int launches) { h->launches_last = launches; }
 
 }  // namespace sbt
 
@@ -476,6 +487,8 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
 {
     sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, oh);
     if (st != SBT_OK || !oh) return st != SBT_OK ? st : SBT_ERR_ARG;
+    if (!host_offsets_valid(event_offsets, n_events, n_hits))
+        return fail(h, SBT_ERR_ARG, "event_offsets must be non-decreasing, from >= 0 to <= n_hits");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!h->copy_in) e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
@@ -738,7 +751,7 @@ sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const flo
 sbt_status sbt_fit_adjoint(sbt_handle* h, const float* x, const float* y, const float* z,
                            const int32_t* module, int32_t n_hits, const int32_t* hit_offsets,
                            const int32_t* track_hits, int32_t n_tracks, const double* align,
-                           double* chi2_sum, double* grad, void* stream)
+                           double* chi2_sum, double* grad, int32_t* skipped, void* stream)
 {
     if (!h) return SBT_ERR_ARG;
     if (h->C.pairs) return fail(h, SBT_ERR_ARG, "the alignment adjoint takes single-plane modules");
@@ -746,13 +759,13 @@ sbt_status sbt_fit_adjoint(sbt_handle* h, const float* x, const float* y, const 
     if (!hit_offsets || !align || !chi2_sum || (n_tracks > 0 && (!track_hits || !x || !y || !z || !module)))
         return fail(h, SBT_ERR_ARG, "NULL argument");
     AdjointWork W;
-    W.blocks = adjoint_blocks();
-    size_t need = sizeof(double) * (size_t)W.blocks * (6 * h->C.M + 1);
+    W.blocks = adjoint_blocks(h->sm_count);
+    size_t need = sizeof(double) * adjoint_partial_entries(h->C.M, W.blocks);
     cudaError_t e = h->misc_arena.reserve(std::max(need, h->misc_arena.bytes));
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint allocation");
     W.partial = (double*)h->misc_arena.base;
     Inputs in = make_inputs(x, y, z, module, nullptr, 0, n_hits);
-    e = launch_adjoint(h->C, in, hit_offsets, track_hits, n_tracks, align, chi2_sum, grad, W,
+    e = launch_adjoint(h->C, in, hit_offsets, track_hits, n_tracks, align, chi2_sum, grad, skipped, W,
                        (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint launch");
     return SBT_OK;

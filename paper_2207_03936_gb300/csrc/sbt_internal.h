@@ -62,9 +62,11 @@ struct Sorted {
 
 // Per-region scratch of the search (a region is an event in the plain launch,
 // a resident block in the persistent launch).  Region r with hit base hb and
-// capacity cap owns per-hit arrays [hb, hb + cap), tracklets from hb/4 + r
-// (cap/4 + 1 entries), final-track records from hb/3 + r (cap/3 + 1 entries)
-// and forming-track slots from forming_base(hb, r) (2 (cap/12 + 72) entries).
+// capacity cap owns per-hit arrays [hb, hb + cap), tracklets from hb + r
+// (cap + 1 entries: every seed has its own middle hit, so an event has at most
+// one tracklet per hit), final-track records from hb/3 + r (cap/3 + 1
+// entries: final tracks are disjoint and have three hits or more) and
+// forming-track slots from forming_base(hb, r) (2 (cap/12 + 72) entries).
 struct Work {
     uint32_t* list;              // seeding work lists
     uint16_t* mark;              // canonical-order marks by input index
@@ -94,7 +96,7 @@ struct Staging {
 };
 
 // Sizes of the scratch arrays for `hits` hit slots over `regions` regions.
-inline int64_t tracklet_entries(int64_t hits, int64_t regions) { return hits / 4 + regions + 1; }
+inline int64_t tracklet_entries(int64_t hits, int64_t regions) { return hits + regions + 1; }
 inline int64_t final_entries(int64_t hits, int64_t regions) { return hits / 3 + regions + 1; }
 
 size_t smem_bytes(int nmax, int threads);
@@ -129,18 +131,20 @@ int persistent_blocks_per_sm(const DevConfig& C, int threads);
 
 // Adjoint (sbt_adjoint.cu).
 struct AdjointWork {
-    double* partial;   // [blocks * (6 M + 1)]
+    double* partial;   // [adjoint_partial_entries(M, blocks)]
     int blocks;
 };
 cudaError_t launch_adjoint(const DevConfig& C, const Inputs& in, const int32_t* hit_offsets,
                            const int32_t* track_hits, int32_t n_tracks, const double* align,
-                           double* chi2_sum, double* grad, const AdjointWork& W,
+                           double* chi2_sum, double* grad, int32_t* skipped, const AdjointWork& W,
                            cudaStream_t stream);
-int adjoint_blocks();
+int adjoint_blocks(int sm_count);
+size_t adjoint_partial_entries(int M, int blocks);
 
 // Handle accessors for translation units that cannot see the handle type.
 const DevConfig& handle_device_config(const sbt_handle* h);
 int handle_plain_threads(const sbt_handle* h);
 void handle_set_error(sbt_handle* h, const std::string& msg);
+void handle_set_launches(sbt_handle* h, int launches);
 
 }  // namespace sbt

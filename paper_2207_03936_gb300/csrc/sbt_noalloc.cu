@@ -37,7 +37,7 @@ constexpr Layout make_layout()
 {
     Layout L{};
     const int64_t H = kNoAllocMaxHits, E = kNoAllocMaxEvents;
-    const int64_t TL = H / 4 + E + 1, FN = H / 3 + E + 1;
+    const int64_t TL = H + E + 1, FN = H / 3 + E + 1;
     size_t o = 0;
     L.coords = o;     o = align256(o + 16 * (size_t)H);
     L.phi = o;        o = align256(o + 2 * (size_t)H);
@@ -70,7 +70,7 @@ constexpr Layout make_layout()
 
 constexpr Layout kLayout = make_layout();
 
-// The workspace (about 40 MB).  In host code this name is only a host-side
+// The workspace (about 45 MB).  In host code this name is only a host-side
 // stand-in: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_workspace[kLayout.total];
 
@@ -79,7 +79,9 @@ std::mutex g_mutex;
 unsigned char* g_device_ptr[kMaxDevices] = {};
 
 // Device address of the workspace on the current device, looked up once per
-// device (the first call on each device does this).
+// device (the first call on each device does this) and kept for the life of
+// the process: a cudaDeviceReset unloads the library's device image, after
+// which the kept address is no longer valid.
 cudaError_t workspace_address(unsigned char** out)
 {
     int dev = 0;
@@ -182,5 +184,6 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
         handle_set_error(h, std::string("noalloc launch: ") + cudaGetErrorString(e));
         return SBT_ERR_CUDA;
     }
+    handle_set_launches(h, n_events > 0 ? 4 : 2);
     return SBT_OK;
 }

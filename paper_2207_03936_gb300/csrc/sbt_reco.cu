@@ -77,20 +77,6 @@ __device__ __forceinline__ int phi_dist(uint32_t u, uint32_t v)
     return d1 < d2 ? d1 : d2;
 }
 
-// First position in phi[0, n) with phi >= v.
-__device__ __forceinline__ int lower_bound16(const uint16_t* phi, int n, uint32_t v)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((uint32_t)phi[mid] < v)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 // Straight-line extrapolation of (a, c) to the plane z = zt.
 __device__ __forceinline__ void extrapolate(float4 A, float4 Cc, float zt, float& xp, float& yp)
 {
@@ -155,20 +141,31 @@ enum Misc {
     kNew = 8, kWork = 9, kMiscN = 32
 };
 
-// Per-block shared memory of the search: flag bits, module offsets, counters.
+// Bucket tables: for a phi-sorted run of hits, tab[k] is the first position
+// whose phi16 >> kTabShift is at least k (tab[kTabBuckets] = the run's
+// length), so a phi lower bound starts inside its bucket instead of at the
+// end of a binary search.
+constexpr int kTabShift = 8;
+constexpr int kTabBuckets = 65536 >> kTabShift;
+constexpr int kTabEntries = kTabBuckets + 1;
+
+// Per-block shared memory of the search: flag bits, module offsets, counters
+// and three bucket tables (the seeding and following target modules, kept
+// as a ring over module parity, and the list of unflagged outer hits).
 // Everything sized by the event lives in global scratch (L1-resident), so a
-// block needs about 2 KB plus n/8 bytes and many events are in flight per SM.
+// block needs about 4 KB plus n/8 bytes and many events are in flight per SM.
 struct Smem {
     uint32_t* flag;     // one bit per sorted position
     int* modoff;
     int* misc;
     int* wsum;          // [33]
+    uint16_t* tab;      // [3][kTabEntries]: module tables by parity, outer list
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct Plan {
-    size_t flag, modoff, misc, wsum, total;
+    size_t flag, modoff, misc, wsum, tab, total;
 };
 
 __host__ __device__ inline Plan make_plan(int nmax, int threads)
@@ -180,6 +177,7 @@ __host__ __device__ inline Plan make_plan(int nmax, int threads)
     p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
     p.misc = o;     o = align16(o + 4 * kMiscN);
     p.wsum = o;     o = align16(o + 4 * 40);
+    p.tab = o;      o = align16(o + 2 * 3 * (size_t)kTabEntries);
     p.total = o;
     return p;
 }
@@ -194,7 +192,35 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
     S.modoff = (int*)(raw + p.modoff);
     S.misc = (int*)(raw + p.misc);
     S.wsum = (int*)(raw + p.wsum);
+    S.tab = (uint16_t*)(raw + p.tab);
     return S;
+}
+
+__device__ __forceinline__ uint16_t* module_tab(const Smem& S, int m) { return S.tab + (m & 1) * kTabEntries; }
+__device__ __forceinline__ uint16_t* outer_tab(const Smem& S) { return S.tab + 2 * kTabEntries; }
+
+// Bucket table of a phi-sorted run of nb hits (key(i) gives phi16 of
+// position i), positions i = first, first + stride, ...: every bucket k is
+// written once, by the position that starts it.
+template <class Key>
+__device__ __forceinline__ void build_tab(uint16_t* tab, int nb, Key key, int first, int stride)
+{
+    for (int i = first; i <= nb; i += stride) {
+        const int klo = i == 0 ? 0 : (int)(key(i - 1) >> kTabShift) + 1;
+        const int khi = i == nb ? kTabBuckets : (int)(key(i) >> kTabShift);
+        for (int k = klo; k <= khi; k++) tab[k] = (uint16_t)i;
+    }
+}
+
+// First position p of the run (0 <= p <= nb) with key(p) >= v.
+template <class Key>
+__device__ __forceinline__ int lower_bound_tab(const uint16_t* tab, Key key, uint32_t v)
+{
+    const int k = (int)(v >> kTabShift);
+    int p = tab[k];
+    const int e = tab[k + 1];
+    while (p < e && key(p) < v) p++;
+    return p;
 }
 
 __device__ __forceinline__ bool flagged(const Smem& S, int p) { return (S.flag[p >> 5] >> (p & 31)) & 1u; }
@@ -266,9 +292,9 @@ __device__ inline Region<HS> region_of(const Sorted& O, int off, const Work& W, 
     R.pos = W.pos + hb;
     R.prev = W.prev + hb;
     R.claim = W.claim + hb;
-    R.tracklets = W.tracklets + hb / 4 + r;
-    R.tl_q = W.tl_q + hb / 4 + r;
-    R.lcap = cap / 4 + 1;
+    R.tracklets = W.tracklets + hb + r;
+    R.tl_q = W.tl_q + hb + r;
+    R.lcap = cap + 1;
     R.finals = W.finals + hb / 3 + r;
     R.fin_rank = W.fin_rank + hb / 3 + r;
     R.fin_start = W.fin_start + hb / 3 + r;
@@ -375,7 +401,9 @@ __device__ void warp_bitonic(uint32_t* a, int s)
 // (module, top six bits of phi16) bucket; each bucket is then sorted by
 // phi16 << 14 | input index, a unique key, so the order is the one of a
 // stable sort by (module, phi16).  Status SBT_ERR_ARG for a module id out of
-// range, SBT_ERR_CAPACITY above the configured hit limit.
+// range or a hit range [offsets[e], offsets[e+1]) that is not inside
+// [0, n_hits) (no later kernel reads or writes anything of such an event),
+// SBT_ERR_CAPACITY above the configured hit limit.
 template <class HS>
 __global__ void __launch_bounds__(kSortThreads, 2) k_sort(DevConfig C, Inputs in, Sorted O)
 {
@@ -391,12 +419,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort(DevConfig C, Inputs in
     const int tid = threadIdx.x;
     const int e = blockIdx.x;
     const int off = in.offsets[e];
-    const int n = in.offsets[e + 1] - off;
-    if (n < 0 || n > C.nmax || (C.gec > 0 && n > C.gec)) {
+    const int64_t n64 = (int64_t)in.offsets[e + 1] - off;
+    const bool range_bad = off < 0 || n64 < 0 || off + n64 > in.n_hits;
+    if (range_bad || n64 > C.nmax || (C.gec > 0 && n64 > C.gec)) {
         if (tid == 0)
-            O.status[e] = n < 0 ? SBT_ERR_ARG : (C.gec > 0 && n > C.gec) ? SBT_EVENT_CUT : SBT_ERR_CAPACITY;
+            O.status[e] = range_bad ? SBT_ERR_ARG : (C.gec > 0 && n64 > C.gec) ? SBT_EVENT_CUT : SBT_ERR_CAPACITY;
         return;
     }
+    const int n = (int)n64;
     for (int b = tid; b < kSortBuckets; b += NT) cnt[b] = 0;
     if (tid == 0) {
         err = 0;
@@ -603,94 +633,46 @@ __device__ __forceinline__ void scan_from(const Smem& S, const Region<HS>& R, in
 }
 
 template <class G, class Better, class Take, class HS>
-__device__ __forceinline__ void scan_window(const Smem& S, const Region<HS>& R, int b0, int nb, float xp,
-                                            float yp, float cut, float sqrt_cut, int plane,
-                                            Better better, Take take)
+__device__ __forceinline__ void scan_window(const Smem& S, const Region<HS>& R, int b0, int nb,
+                                            const uint16_t* tab, float xp, float yp, float cut,
+                                            float sqrt_cut, int plane, Better better, Take take)
 {
     if (nb <= 0) return;
     uint32_t lo, width;
     const bool windowed = window_of(xp, yp, cut, sqrt_cut, lo, width);
-    const int lo_idx = windowed ? lower_bound16(R.phi + b0, nb, lo) : 0;
+    const uint16_t* phi = R.phi + b0;
+    const int lo_idx = windowed ? lower_bound_tab(tab, [&](int i) { return (uint32_t)phi[i]; }, lo) : 0;
     scan_from<G>(S, R, b0, nb, xp, yp, cut, windowed, lo_idx, lo, width, plane, better, take);
 }
 
-// First index in keys[0, n) whose upper 16 bits are >= v.
-__device__ __forceinline__ int lower_bound_hi16(const uint32_t* keys, int n, uint32_t v)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((keys[mid] >> 16) < v)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
-constexpr int kSeedBatch = 1;
-
-// Candidates a[0, na) of one middle hit, processed together: extrapolations
-// to each plane of module i, then the binary searches of their windows in
-// lockstep (independent loads in flight), then the window scans.  Keeps the
-// best (scatter, a, b).
+// Candidates a[0, na) of one middle hit: extrapolation to each plane of
+// module i, the window's start from the module's bucket table, then the
+// window scan.  Keeps the best (scatter, a, b).
 template <class G, class HS>
-__device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& S, const Region<HS>& R,
-                                                int i, int i0, int ni, float4 Cc, float sqrt_cut,
-                                                const int* a, int na, bool& have, float& best_sc,
-                                                int& best_a, int& best_b)
+__device__ __forceinline__ void seed_candidate(const DevConfig& C, const Smem& S, const Region<HS>& R,
+                                               int i, int i0, int ni, float4 Cc, float sqrt_cut, int au,
+                                               bool& have, float& best_sc, int& best_a, int& best_b)
 {
+    const float4 A = R.coords[au];
+    const uint16_t* tab = module_tab(S, i);
+    const uint16_t* phi = R.phi + i0;
     for (int plane = 0; plane < G::kPlanes; plane++) {
-        const float zi = G::z(C, i, plane);
-        float xp[kSeedBatch], yp[kSeedBatch];
-        uint32_t lo[kSeedBatch], width[kSeedBatch];
-        int L[kSeedBatch], H[kSeedBatch];
-        bool win[kSeedBatch];
-#pragma unroll
-        for (int u = 0; u < kSeedBatch; u++) {
-            L[u] = 0;
-            H[u] = 0;
-            win[u] = false;
-            if (u < na) {
-                extrapolate(R.coords[a[u]], Cc, zi, xp[u], yp[u]);
-                win[u] = window_of(xp[u], yp[u], C.S_seed, sqrt_cut, lo[u], width[u]);
-                H[u] = win[u] ? ni : 0;
-            }
-        }
-        const uint16_t* phi = R.phi + i0;
-        for (int it = 0; it < 17; it++) {
-            bool active = false;
-#pragma unroll
-            for (int u = 0; u < kSeedBatch; u++) active |= L[u] < H[u];
-            if (!active) break;
-#pragma unroll
-            for (int u = 0; u < kSeedBatch; u++) {
-                if (L[u] < H[u]) {
-                    const int mid = (L[u] + H[u]) >> 1;
-                    if ((uint32_t)phi[mid] < lo[u])
-                        L[u] = mid + 1;
-                    else
-                        H[u] = mid;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kSeedBatch; u++) {
-            if (u >= na) continue;
-            const int au = a[u];
-            scan_from<G>(
-                S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u], plane,
-                [&](float sc, int b) {
-                    return !have || sc < best_sc ||
-                           (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
-                },
-                [&](float sc, int b) {
-                    have = true;
-                    best_sc = sc;
-                    best_a = au;
-                    best_b = b;
-                });
-        }
+        float xp, yp;
+        uint32_t lo, width;
+        extrapolate(A, Cc, G::z(C, i, plane), xp, yp);
+        const bool win = window_of(xp, yp, C.S_seed, sqrt_cut, lo, width);
+        const int L = win ? lower_bound_tab(tab, [&](int k) { return (uint32_t)phi[k]; }, lo) : 0;
+        scan_from<G>(
+            S, R, i0, ni, xp, yp, C.S_seed, win, L, lo, width, plane,
+            [&](float sc, int b) {
+                return !have || sc < best_sc || (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
+            },
+            [&](float sc, int b) {
+                have = true;
+                best_sc = sc;
+                best_a = au;
+                best_b = b;
+            });
     }
 }
 
@@ -709,14 +691,12 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
     if (nu <= 0 || ni <= 0) return false;
     const uint32_t phc = R.phi[c];
     const float4 Cc = R.coords[c];
-    const int j = lower_bound_hi16(outer, nu, phc);
+    const int j = lower_bound_tab(outer_tab(S), [&](int k) { return outer[k] >> 16; }, phc);
     int up = j, dn = j - 1;
     int found = 0, dK = INT_MAX;
     bool have = false;
     float best_sc = 0.0f;
     int best_a = 0, best_b = 0;
-    int cand[kSeedBatch];
-    int nc = 0;
     for (int visited = 0; visited < nu; visited++) {
         const int iu = up >= nu ? up - nu : up;
         const int id = dn < 0 ? dn + nu : dn;
@@ -736,14 +716,8 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
         if (found >= C.K && d > dK) break;
         found++;
         if (found == C.K) dK = d;
-        cand[nc++] = a;
-        if (nc == kSeedBatch) {
-            seed_candidates<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
-            nc = 0;
-        }
+        seed_candidate<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, a, have, best_sc, best_a, best_b);
     }
-    if (nc > 0)
-        seed_candidates<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
     if (have) {
         oa = best_a;
         ob = best_b;
@@ -765,7 +739,7 @@ __device__ bool follow_best(const DevConfig& C, const Smem& S, const Region<HS>&
         float xp, yp;
         extrapolate(A, Cc, G::z(C, t, plane), xp, yp);
         scan_window<G>(
-            S, R, b0, nb, xp, yp, C.S_follow, sqrt_cut, plane,
+            S, R, b0, nb, module_tab(S, t), xp, yp, C.S_follow, sqrt_cut, plane,
             [&](float sc, int b) { return !have || sc < best || (sc == best && b < bb); },
             [&](float sc, int b) {
                 have = true;
@@ -889,6 +863,13 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
         }
         if (s + 3 <= M - 1)  // claim words of the target module start empty
             for (int p = S.modoff[s + 3] + tid; p < S.modoff[s + 4]; p += NT) R.claim[p] = ~0ull;
+        // bucket tables of the modules searched in this step: s+2 (seeding;
+        // built in the previous step as its following target) and s+3
+        for (int m = s == 0 ? 2 : 3 + s; m <= min(s + 3, M - 1); m++) {
+            const uint16_t* ph = R.phi + S.modoff[m];
+            build_tab(module_tab(S, m), S.modoff[m + 1] - S.modoff[m],
+                      [&](int i) { return (uint32_t)ph[i]; }, tid, NT);
+        }
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
         uint32_t* outer = list + (c1 - c0);
         for (int base = c0 + (tid & ~31); base < c1; base += NT) {
@@ -913,6 +894,8 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
                 nu += __popc(m);
             }
             if (lane == 0) misc[kNOuter] = nu;
+            __syncwarp();
+            build_tab(outer_tab(S), nu, [&](int i) { return outer[i] >> 16; }, lane, 32);
         }
         __syncthreads();
         const int nl = misc[kList];

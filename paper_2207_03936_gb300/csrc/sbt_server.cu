@@ -167,10 +167,13 @@ struct Slot {
     HostBuf<int32_t> hm, hoff;
 };
 
-// Device bytes one batch needs (inputs, outputs and the plain workspace).
+// Device bytes one batch needs (inputs, outputs and the plain workspace):
+// per hit 16 B inputs, 18 B sorted hits, about 45 B search scratch (claims,
+// links, lists, tracklets, forming and final tracks), about 12 B staging and
+// about 13 B outputs, rounded up.
 int64_t batch_bytes(int64_t hits, int64_t events)
 {
-    return hits * 96 + events * 320 + (1 << 16);
+    return hits * 112 + events * 320 + (1 << 16);
 }
 
 }  // namespace
@@ -495,6 +498,10 @@ sbt_status sbt_server_submit_schedule(sbt_server* S, const float* x, const float
                                       int32_t n_events, const double* arrival_s, int64_t first_id)
 {
     if (!S || n_events < 0 || !event_offsets || !arrival_s) return SBT_ERR_ARG;
+    if (event_offsets[0] < 0) return SBT_ERR_ARG;
+    for (int32_t e = 0; e < n_events; e++)
+        if (event_offsets[e] > event_offsets[e + 1]) return SBT_ERR_ARG;
+    if (event_offsets[n_events] > 0 && (!x || !y || !z || !module)) return SBT_ERR_ARG;
     if (S->stop.load()) return SBT_ERR_STATE;
     if (S->feeder.joinable()) S->feeder.join();
     {

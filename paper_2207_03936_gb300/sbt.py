@@ -77,7 +77,7 @@ def lib() -> ctypes.CDLL:
             "sbt_reconstruct_batched": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
             "sbt_reconstruct_host": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
             "sbt_autotune": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
-            "sbt_fit_adjoint": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P, _P, _P, _P]),
+            "sbt_fit_adjoint": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P, _P, _P, _P, _P]),
             "sbt_debug_sort": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P]),
             "sbt_debug_phi16": (_I32, [_P, _P, _I32, _P, _P]),
             "sbt_last_launch_count": (_I32, [_P]),
@@ -296,19 +296,25 @@ def sbt_profile_batched(h: Handle, x, y, z, module, event_offsets, out: TrackOut
 
 
 def sbt_fit_adjoint(h: Handle, x, y, z, module, hit_offsets, track_hits, align,
-                    want_grad=True, stream=None):
-    """(chi2_sum [1] fp64, grad [n_modules, 6] fp64 or None) as CUDA tensors."""
+                    want_grad=True, stream=None, with_skipped=False):
+    """(chi2_sum [1] fp64, grad [n_modules, 6] fp64 or None) as CUDA tensors;
+    with_skipped adds the number of tracks without a straight-line fit or
+    with an index out of range ([1] int32), which contribute nothing."""
     f32, i32, f64 = torch.float32, torch.int32, torch.float64
     chi2 = torch.zeros(1, dtype=f64, device=x.device)
     grad = torch.zeros(h.n_modules * 6, dtype=f64, device=x.device) if want_grad else None
+    skipped = torch.zeros(1, dtype=i32, device=x.device) if with_skipped else None
     st = lib().sbt_fit_adjoint(h.h, _ptr(x, f32, "x"), _ptr(y, f32, "y"), _ptr(z, f32, "z"),
                                _ptr(module, i32, "module"), x.numel(),
                                _ptr(hit_offsets, i32, "hit_offsets"),
                                _ptr(track_hits, i32, "track_hits"), hit_offsets.numel() - 1,
                                _ptr(align.contiguous(), f64, "align"), _ptr(chi2, f64, "chi2"),
-                               _ptr(grad, f64, "grad") if grad is not None else None, _stream(stream))
+                               _ptr(grad, f64, "grad") if grad is not None else None,
+                               _ptr(skipped, i32, "skipped") if skipped is not None else None,
+                               _stream(stream))
     _check(st, h.h)
-    return chi2, (grad.view(h.n_modules, 6) if grad is not None else None)
+    res = (chi2, (grad.view(h.n_modules, 6) if grad is not None else None))
+    return res + (skipped,) if with_skipped else res
 
 
 def sbt_debug_sort(h: Handle, x, y, module, event_offsets, stream=None):

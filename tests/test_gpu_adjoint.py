@@ -95,3 +95,34 @@ def test_adjoint_on_reconstructed_tracks(setup):
     assert abs(float(c.item()) - v) <= 1e-12 * v
     # the fp64 objective at zero alignment equals the sum of the fp32 fits
     assert abs(v - float(r["chi2"].astype(np.float64).sum())) <= 1e-3 * v
+
+
+def test_adjoint_on_long_repeated_and_invalid_tracks(setup):
+    # tracks of 104 hits (two per module), a repeated module, and tracks
+    # without a line fit or with indices out of range (skipped and counted):
+    # the same value, gradient and count as the oracle's
+    sbt, h, _, _, _, _ = setup
+    from tests.hand_events import MZ
+    from tests.test_oracle_alignment import _odd_tracks
+    x, y, z, m, good = _odd_tracks()
+    x, y, z = (np.append(a, np.float32(a[0])) for a in (x, y, z))
+    m = np.append(m, np.int32(52))
+    bad = [np.array([11]), np.array([], np.int64), np.array([5, 5 + 52]), np.array([1, 2, 105]),
+           np.array([58, 59, 104, 61])]
+    allt = [good[0], bad[0], good[1], bad[1], bad[2], good[2], bad[3], bad[4]] * 40
+    th = np.concatenate(allt).astype(np.int32)
+    ho = np.concatenate([[0], np.cumsum([len(t) for t in allt])]).astype(np.int32)
+    rng = np.random.default_rng(21)
+    align = np.concatenate([rng.normal(0, 0.005, (52, 3)), rng.normal(0, 5e-5, (52, 3))], 1)
+    d = [torch.from_numpy(a).cuda() for a in (x, y, z, m, ho, th)]
+    c, g, sk = sbt.sbt_fit_adjoint(h, *d, torch.from_numpy(align).cuda(), with_skipped=True)
+    torch.cuda.synchronize()
+    v, go, so = oracle.align_chi2(x, y, z, m, ho, th, MZ, align, SIGMA, count_skipped=True)
+    assert int(sk.item()) == so == 5 * 40
+    assert abs(float(c.item()) - v) <= 1e-12 * v
+    g = g.cpu().numpy()
+    scale = np.abs(go).max()
+    assert (np.abs(g - go) <= 1e-9 * np.maximum(np.abs(go), 1e-3 * scale)).all()
+    # reproducible to the bit with the repeated-module path taken
+    c2, g2, _ = sbt.sbt_fit_adjoint(h, *d, torch.from_numpy(align).cuda(), with_skipped=True)
+    assert torch.equal(c.cpu(), c2.cpu()) and np.array_equal(g, g2.cpu().numpy())

@@ -537,3 +537,32 @@ def test_crowded_tiny_events_bit_exact(sbt, cfg_seed):
             assert_same(run_gpu(sbt, h, ev, batched), o)
     finally:
         h.close()
+
+
+def test_event_ranges_outside_the_hits_are_reported(sbt, handle):
+    # events whose hit range ends past n_hits get SBT_ERR_ARG on the device
+    # and no tracks; the others are reconstructed as usual.  The hit arrays
+    # passed are views of the whole batch, so memory behind n_hits exists and
+    # a missing check could not read outside an allocation.
+    ev = synth.make_events(2, 6, workers=1)
+    off = ev.event_offsets
+    H = int(off[4]) + 10                       # event 4 ends past H, event 5 lies beyond it
+    full = to_dev(ev)
+    dev = [a[:H] for a in full[:4]] + [full[4]]
+    sub = ev.subset(0, 4)
+    o = oracle_of(sub)
+    for fn in (sbt.sbt_reconstruct, sbt.sbt_reconstruct_batched):
+        g = fn(handle, *dev).compact()
+        torch.cuda.synchronize()
+        assert list(g["event_status"]) == [0, 0, 0, 0, 1, 1]
+        assert int(g["counts"][3]) == 2 and int(g["counts"][2]) == 0
+        t4 = int(g["track_offsets"][4])
+        assert t4 == o.n_tracks and int(g["track_offsets"][6]) == t4
+        assert np.array_equal(g["hit_offsets"][:t4 + 1], o.hit_offsets)
+        assert np.array_equal(g["track_hits"][:int(o.hit_offsets[-1])], o.track_hits)
+        assert np.array_equal(g["params"][:t4].view(np.uint32), o.params.view(np.uint32))
+    # the host entry point sees the offsets on the host and refuses the call
+    host = [torch.from_numpy(np.ascontiguousarray(a[:H])) for a in (ev.x, ev.y, ev.z, ev.module)]
+    out = sbt.TrackOutput.allocate(6, H, pin_memory=True)
+    with pytest.raises(sbt.SbtError, match="non-decreasing"):
+        sbt.sbt_reconstruct_host(handle, *host, torch.from_numpy(off), out=out)

@@ -40,3 +40,34 @@ def test_noalloc_matches_reconstruct_twice():
             sbt.sbt_reconstruct_noalloc(h, x, x, x, m, off, out=out)
     finally:
         h.close()
+
+
+def test_noalloc_near_its_limits_allocates_nothing():
+    # 4096 small events (one vertex, Poisson(6) tracks) totalling 99.6% of
+    # the 2^19 hits: the fixed workspace at the edge of both limits.  The
+    # result must equal sbt_reconstruct's, and the device's free memory must
+    # not move across two calls (after one call that loads the kernels).
+    from paper_2207_03936_gb300 import sbt
+    ev = synth.generate(synth.Recipe(n_events=4096, pv_mode="fixed", pv_mean=1, tracks_per_pv=6.0,
+                                     seed=3), workers=1)
+    assert ev.n_events == 4096 and 0.99 * (1 << 19) < ev.n_hits <= 1 << 19
+    dev = [torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z, ev.module, ev.event_offsets)]
+    h = sbt.sbt_create(ev.module_z, sbt.default_config())
+    try:
+        ref = sbt.sbt_reconstruct(h, *dev).compact()
+        assert (ref["event_status"] == 0).all() and ref["counts"][0] > 20000
+        outs = [sbt.TrackOutput.allocate(ev.n_events, ev.n_hits) for _ in range(2)]
+        sbt.sbt_reconstruct_noalloc(h, *dev, out=outs[0])
+        torch.cuda.synchronize()
+        assert h.last_launch_count() == 4
+        free0 = torch.cuda.mem_get_info()[0]
+        for out in outs:
+            sbt.sbt_reconstruct_noalloc(h, *dev, out=out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        for out in outs:
+            got = out.compact()
+            for k, v in ref.items():
+                assert np.array_equal(got[k], v), k
+    finally:
+        h.close()
