@@ -612,7 +612,7 @@ def main():
                          "peak_kind": peak_kind,
                          "kernel": "k_search_persistent", "kernel_ms": kms[2],
                          "kernel_ms_all": {"order": kms[0], "sort": kms[1], "search": kms[2],
-                                           "scan": kms[3], "consolidate": kms[4]},
+                                           "scan": kms[3], "output": kms[4]},
                          "sort_kernel": {"achieved_gbs": sort_gbs, "frac": sort_gbs / peak,
                                          "traffic": profiled_traffic("k_sort", ev.n_hits),
                                          "issue": issue_roofline("k_sort", ev.n_hits, kms[1], sm_mhz, sm_count)},

@@ -81,16 +81,12 @@ size_t carve_work(void* base, int64_t hits, int64_t regions, Work* W)
     Carver c(base);
     Work w;
     w.list = c.take<uint32_t>(hits);
-    w.mark = c.take<uint16_t>(hits);
-    w.pos = c.take<uint16_t>(hits);
     w.prev = c.take<uint16_t>(hits);
     w.claim = c.take<unsigned long long>(hits);
     w.ft = c.take<FTrack>(forming_entries(hits, regions));
     w.tracklets = c.take<unsigned long long>(tracklet_entries(hits, regions));
     w.tl_q = c.take<uint32_t>(tracklet_entries(hits, regions));
     w.finals = c.take<uint32_t>(final_entries(hits, regions));
-    w.fin_rank = c.take<int32_t>(final_entries(hits, regions));
-    w.fin_start = c.take<int32_t>(final_entries(hits, regions));
     if (W) *W = w;
     return c.off + 256;
 }
@@ -112,10 +108,10 @@ size_t carve_staging(void* base, int64_t n_hits, int64_t n_events, Staging* S)
 {
     Carver c(base);
     Staging s;
-    s.hits = c.take<int32_t>(n_hits);
-    s.len = c.take<uint8_t>(n_hits / 3 + n_events + 1);
-    s.fit = c.take<float4>(n_hits / 3 + n_events + 1);
-    s.chi2 = c.take<float>(n_hits / 3 + n_events + 1);
+    s.hits = c.take<float4>(n_hits);
+    s.tkey = c.take<int32_t>(n_hits / 3 + n_events + 1);
+    s.tinfo = c.take<uint32_t>(n_hits / 3 + n_events + 1);
+    s.rinfo = c.take<uint32_t>(n_hits / 3 + n_events + 1);
     s.ev_ntracks = c.take<int32_t>(n_events);
     s.ev_nhits = c.take<int32_t>(n_events);
     s.track_base = c.take<int32_t>(n_events);
@@ -251,7 +247,7 @@ sbt_status ensure_persistent(sbt_handle* h, int blocks, Work* W)
     return SBT_OK;
 }
 
-// Enqueue the batched sequence (order, sort, persistent search, scan, consolidation).
+// Enqueue the batched sequence (order, sort, persistent search, scan, output).
 sbt_status enqueue_batched(sbt_handle* h, const Inputs& in, const Sorted& O, const Staging& S,
                            const Work& W, const sbt_tracks& out, int threads, int blocks,
                            cudaStream_t st)
@@ -586,9 +582,9 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
         Oc.modoff = O.modoff + ev0 * (h->C.M + 1);
         Oc.status = O.status + ev0;
         Sc = S;
-        Sc.len = S.len + ev0;  // slot off/3 + event: the chunk-local event index plus e0[c]
-        Sc.fit = S.fit + ev0;
-        Sc.chi2 = S.chi2 + ev0;
+        Sc.tkey = S.tkey + ev0;  // slot off/3 + event: the chunk-local event index plus e0[c]
+        Sc.tinfo = S.tinfo + ev0;
+        Sc.rinfo = S.rinfo + ev0;
         Sc.ev_ntracks = S.ev_ntracks + ev0;
         Sc.ev_nhits = S.ev_nhits + ev0;
         Sc.track_base = S.track_base + ev0;
@@ -833,7 +829,7 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
         if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
         if (e == cudaSuccess) e = launch_scan(in, S, *out, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
-        if (e == cudaSuccess) e = launch_consolidate(h->C, in, S, *out, s);
+        if (e == cudaSuccess) e = launch_output(h->C, in, S, *out, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
         for (int k = 0; k < 5 && e == cudaSuccess; k++) {

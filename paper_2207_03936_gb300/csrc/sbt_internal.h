@@ -69,24 +69,24 @@ struct Sorted {
 // forming-track slots from forming_base(hb, r) (2 (cap/12 + 72) entries).
 struct Work {
     uint32_t* list;              // seeding work lists
-    uint16_t* mark;              // canonical-order marks by input index
-    uint16_t* pos;               // track hit positions in output order
     uint16_t* prev;              // previous hit of a track, by sorted position
     unsigned long long* claim;   // hit claims (tagged keys), by sorted position
     FTrack* ft;                  // forming tracks, two buffers
     unsigned long long* tracklets;
     uint32_t* tl_q;
     uint32_t* finals;            // last hit | nhits << 16
-    int32_t* fin_rank;
-    int32_t* fin_start;
 };
 
-// Per-event staging of the search output, consumed by the consolidation.
+// Per-event results of the search, consumed by the output kernel.  Track
+// records of event e start at slot off/3 + e (an event has at most n/3
+// tracks: they are disjoint and have three hits or more).
 struct Staging {
-    int32_t* hits;        // [n_hits]: event e writes from event_offsets[e]
-    uint8_t* len;         // [n_hits / 3 + n_events + 1]: event e from off/3 + e
-    float4* fit;          // same indexing as len: (x0, y0, tx, ty) per track
-    float* chi2;          // same indexing as len
+    float4* hits;         // [n_hits]: event e from event_offsets[e], each track's hit records
+                          // contiguous in traversal order, tracks in found order
+                          // (x, y, z as stored, event-local input index as int bits)
+    int32_t* tkey;        // [n_hits / 3 + n_events + 1] smallest input index of each found track
+    uint32_t* tinfo;      // same indexing: first staged hit | hits << 16, found order
+    uint32_t* rinfo;      // same indexing: tinfo of the track of each rank (output kernel)
     int32_t* ev_ntracks;  // [n_events]
     int32_t* ev_nhits;    // [n_events]
     int32_t* track_base;  // [n_events]
@@ -110,12 +110,13 @@ cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream
 cudaError_t launch_persistent(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                               const Staging& S, const sbt_tracks& out, int threads, int blocks,
                               cudaStream_t stream);
+// Scan of the per-event counts, then the output kernel (CSR hit lists and fits).
 cudaError_t launch_finish(const DevConfig& C, const Inputs& in, const Staging& S,
                           const sbt_tracks& out, cudaStream_t stream);
 cudaError_t launch_scan(const Inputs& in, const Staging& S, const sbt_tracks& out,
                         cudaStream_t stream);
-cudaError_t launch_consolidate(const DevConfig& C, const Inputs& in, const Staging& S,
-                               const sbt_tracks& out, cudaStream_t stream);
+cudaError_t launch_output(const DevConfig& C, const Inputs& in, const Staging& S,
+                          const sbt_tracks& out, cudaStream_t stream);
 cudaError_t launch_debug_sort_copy(const DevConfig& C, const Inputs& in, const Sorted& O,
                                    uint16_t* phi16, int32_t* perm, int32_t* module_offsets,
                                    cudaStream_t stream);

@@ -29,8 +29,8 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // kNoAllocMaxHits hits and kNoAllocMaxEvents events), each 256-byte aligned.
 struct Layout {
     size_t coords, phi, modoff, status;
-    size_t list, mark, pos, prev, claim, ft, tracklets, tl_q, finals, fin_rank, fin_start;
-    size_t hits, len, fit, chi2, ntracks, nhits, track_base, hit_base, order, queue, total;
+    size_t list, prev, claim, ft, tracklets, tl_q, finals;
+    size_t hits, tkey, tinfo, rinfo, ntracks, nhits, track_base, hit_base, order, queue, total;
 };
 
 constexpr Layout make_layout()
@@ -44,20 +44,16 @@ constexpr Layout make_layout()
     L.modoff = o;     o = align256(o + 4 * (size_t)E * (kMaxModules + 1));
     L.status = o;     o = align256(o + 4 * (size_t)E);
     L.list = o;       o = align256(o + 4 * (size_t)H);
-    L.mark = o;       o = align256(o + 2 * (size_t)H);
-    L.pos = o;        o = align256(o + 2 * (size_t)H);
     L.prev = o;       o = align256(o + 2 * (size_t)H);
     L.claim = o;      o = align256(o + 8 * (size_t)H);
     L.ft = o;         o = align256(o + 16 * (size_t)(2 * (H / 12 + 72 * E) + 2));
     L.tracklets = o;  o = align256(o + 8 * (size_t)TL);
     L.tl_q = o;       o = align256(o + 4 * (size_t)TL);
     L.finals = o;     o = align256(o + 4 * (size_t)FN);
-    L.fin_rank = o;   o = align256(o + 4 * (size_t)FN);
-    L.fin_start = o;  o = align256(o + 4 * (size_t)FN);
-    L.hits = o;       o = align256(o + 4 * (size_t)H);
-    L.len = o;        o = align256(o + (size_t)(H / 3 + E + 1));
-    L.fit = o;        o = align256(o + 16 * (size_t)(H / 3 + E + 1));
-    L.chi2 = o;       o = align256(o + 4 * (size_t)(H / 3 + E + 1));
+    L.hits = o;       o = align256(o + 16 * (size_t)H);
+    L.tkey = o;       o = align256(o + 4 * (size_t)(H / 3 + E + 1));
+    L.tinfo = o;      o = align256(o + 4 * (size_t)(H / 3 + E + 1));
+    L.rinfo = o;      o = align256(o + 4 * (size_t)(H / 3 + E + 1));
     L.ntracks = o;    o = align256(o + 4 * (size_t)E);
     L.nhits = o;      o = align256(o + 4 * (size_t)E);
     L.track_base = o; o = align256(o + 4 * (size_t)E);
@@ -142,21 +138,17 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     O.status = (int32_t*)(base + L.status);
     Work W;
     W.list = (uint32_t*)(base + L.list);
-    W.mark = (uint16_t*)(base + L.mark);
-    W.pos = (uint16_t*)(base + L.pos);
     W.prev = (uint16_t*)(base + L.prev);
     W.claim = (unsigned long long*)(base + L.claim);
     W.ft = (FTrack*)(base + L.ft);
     W.tracklets = (unsigned long long*)(base + L.tracklets);
     W.tl_q = (uint32_t*)(base + L.tl_q);
     W.finals = (uint32_t*)(base + L.finals);
-    W.fin_rank = (int32_t*)(base + L.fin_rank);
-    W.fin_start = (int32_t*)(base + L.fin_start);
     Staging S;
-    S.hits = (int32_t*)(base + L.hits);
-    S.len = (uint8_t*)(base + L.len);
-    S.fit = (float4*)(base + L.fit);
-    S.chi2 = (float*)(base + L.chi2);
+    S.hits = (float4*)(base + L.hits);
+    S.tkey = (int32_t*)(base + L.tkey);
+    S.tinfo = (uint32_t*)(base + L.tinfo);
+    S.rinfo = (uint32_t*)(base + L.rinfo);
     S.ev_ntracks = (int32_t*)(base + L.ntracks);
     S.ev_nhits = (int32_t*)(base + L.nhits);
     S.track_base = (int32_t*)(base + L.track_base);
@@ -164,9 +156,9 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     S.order = (int32_t*)(base + L.order);
     S.queue = (int32_t*)(base + L.queue);
     // Every array the kernels read is written earlier in the same call (sorted
-    // hits and status by the sort kernel, claims and marks per event before
-    // they are used, counts per event before the scan), so nothing needs
-    // clearing between calls.
+    // hits and status by the sort kernel, claims per event before they are
+    // used, staged hit lists and counts per event before the scan and the
+    // output kernel read them), so nothing needs clearing between calls.
     Inputs in;
     in.x = x;
     in.y = y;

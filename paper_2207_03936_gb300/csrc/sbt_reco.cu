@@ -12,11 +12,12 @@
 //      one-round claims on the hits, flags, and termination after two misses
 //      (section "Track seeding and track following"); barriers separate the
 //      stages as the paper's flagged-hits dependency requires;
-//      then the tracklet filter (section "Tracklet filter"), canonical
-//      ordering of the tracks by smallest input hit index, staging of their
-//      hit lists and the least-squares fit of every track.
-// A device-wide scan and a consolidation kernel then build the CSR output
-// from the staged hit lists and fits (section "Results", data consolidation).
+//      then the tracklet filter (section "Tracklet filter") and staging of
+//      every track's hit records with its smallest input hit index.
+// A device-wide scan and the output kernel then build the CSR output (section
+// "Results", data consolidation): canonical ordering of each event's tracks
+// by smallest input hit index, their hit lists and the least-squares fit of
+// every track, outside the latency-bound search blocks.
 //
 // Decision arithmetic is fp32 with every operation rounded as written
 // (explicit _rn intrinsics, no contraction), so that the result is the
@@ -75,6 +76,20 @@ __device__ __forceinline__ int phi_dist(uint32_t u, uint32_t v)
     int d1 = (int)((u - v) & 0xFFFFu);
     int d2 = (int)((v - u) & 0xFFFFu);
     return d1 < d2 ? d1 : d2;
+}
+
+// First position in phi[0, n) with phi >= v.
+__device__ __forceinline__ int lower_bound16(const uint16_t* phi, int n, uint32_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((uint32_t)phi[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
 }
 
 // Straight-line extrapolation of (a, c) to the plane z = zt.
@@ -141,31 +156,20 @@ enum Misc {
     kNew = 8, kWork = 9, kMiscN = 32
 };
 
-// Bucket tables: for a phi-sorted run of hits, tab[k] is the first position
-// whose phi16 >> kTabShift is at least k (tab[kTabBuckets] = the run's
-// length), so a phi lower bound starts inside its bucket instead of at the
-// end of a binary search.
-constexpr int kTabShift = 8;
-constexpr int kTabBuckets = 65536 >> kTabShift;
-constexpr int kTabEntries = kTabBuckets + 1;
-
-// Per-block shared memory of the search: flag bits, module offsets, counters
-// and three bucket tables (the seeding and following target modules, kept
-// as a ring over module parity, and the list of unflagged outer hits).
+// Per-block shared memory of the search: flag bits, module offsets, counters.
 // Everything sized by the event lives in global scratch (L1-resident), so a
-// block needs about 4 KB plus n/8 bytes and many events are in flight per SM.
+// block needs about 2 KB plus n/8 bytes and many events are in flight per SM.
 struct Smem {
     uint32_t* flag;     // one bit per sorted position
     int* modoff;
     int* misc;
     int* wsum;          // [33]
-    uint16_t* tab;      // [3][kTabEntries]: module tables by parity, outer list
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct Plan {
-    size_t flag, modoff, misc, wsum, tab, total;
+    size_t flag, modoff, misc, wsum, total;
 };
 
 __host__ __device__ inline Plan make_plan(int nmax, int threads)
@@ -177,7 +181,6 @@ __host__ __device__ inline Plan make_plan(int nmax, int threads)
     p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
     p.misc = o;     o = align16(o + 4 * kMiscN);
     p.wsum = o;     o = align16(o + 4 * 40);
-    p.tab = o;      o = align16(o + 2 * 3 * (size_t)kTabEntries);
     p.total = o;
     return p;
 }
@@ -192,35 +195,7 @@ __device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
     S.modoff = (int*)(raw + p.modoff);
     S.misc = (int*)(raw + p.misc);
     S.wsum = (int*)(raw + p.wsum);
-    S.tab = (uint16_t*)(raw + p.tab);
     return S;
-}
-
-__device__ __forceinline__ uint16_t* module_tab(const Smem& S, int m) { return S.tab + (m & 1) * kTabEntries; }
-__device__ __forceinline__ uint16_t* outer_tab(const Smem& S) { return S.tab + 2 * kTabEntries; }
-
-// Bucket table of a phi-sorted run of nb hits (key(i) gives phi16 of
-// position i), positions i = first, first + stride, ...: every bucket k is
-// written once, by the position that starts it.
-template <class Key>
-__device__ __forceinline__ void build_tab(uint16_t* tab, int nb, Key key, int first, int stride)
-{
-    for (int i = first; i <= nb; i += stride) {
-        const int klo = i == 0 ? 0 : (int)(key(i - 1) >> kTabShift) + 1;
-        const int khi = i == nb ? kTabBuckets : (int)(key(i) >> kTabShift);
-        for (int k = klo; k <= khi; k++) tab[k] = (uint16_t)i;
-    }
-}
-
-// First position p of the run (0 <= p <= nb) with key(p) >= v.
-template <class Key>
-__device__ __forceinline__ int lower_bound_tab(const uint16_t* tab, Key key, uint32_t v)
-{
-    const int k = (int)(v >> kTabShift);
-    int p = tab[k];
-    const int e = tab[k + 1];
-    while (p < e && key(p) < v) p++;
-    return p;
 }
 
 __device__ __forceinline__ bool flagged(const Smem& S, int p) { return (S.flag[p >> 5] >> (p & 31)) & 1u; }
@@ -266,16 +241,12 @@ struct Region {
     HitArr<HS> coords;
     const uint16_t* phi;
     uint32_t* list;
-    uint16_t* mark;
-    uint16_t* pos;
     uint16_t* prev;
     unsigned long long* claim;
     unsigned long long* tracklets;
     uint32_t* tl_q;
     int lcap;
     uint32_t* finals;
-    int32_t* fin_rank;
-    int32_t* fin_start;
     FTrack* ft;         // buffer b starts at ft + b * fstride
     int fstride;
 };
@@ -288,16 +259,12 @@ __device__ inline Region<HS> region_of(const Sorted& O, int off, const Work& W, 
     R.coords = HitArr<HS>{(const typename HS::T*)O.coords + off};
     R.phi = O.phi + off;
     R.list = W.list + hb;
-    R.mark = W.mark + hb;
-    R.pos = W.pos + hb;
     R.prev = W.prev + hb;
     R.claim = W.claim + hb;
     R.tracklets = W.tracklets + hb + r;
     R.tl_q = W.tl_q + hb + r;
     R.lcap = cap + 1;
     R.finals = W.finals + hb / 3 + r;
-    R.fin_rank = W.fin_rank + hb / 3 + r;
-    R.fin_start = W.fin_start + hb / 3 + r;
     R.ft = W.ft + forming_base(hb, r);
     R.fstride = cap / 12 + 72;
     return R;
@@ -633,46 +600,94 @@ __device__ __forceinline__ void scan_from(const Smem& S, const Region<HS>& R, in
 }
 
 template <class G, class Better, class Take, class HS>
-__device__ __forceinline__ void scan_window(const Smem& S, const Region<HS>& R, int b0, int nb,
-                                            const uint16_t* tab, float xp, float yp, float cut,
-                                            float sqrt_cut, int plane, Better better, Take take)
+__device__ __forceinline__ void scan_window(const Smem& S, const Region<HS>& R, int b0, int nb, float xp,
+                                            float yp, float cut, float sqrt_cut, int plane,
+                                            Better better, Take take)
 {
     if (nb <= 0) return;
     uint32_t lo, width;
     const bool windowed = window_of(xp, yp, cut, sqrt_cut, lo, width);
-    const uint16_t* phi = R.phi + b0;
-    const int lo_idx = windowed ? lower_bound_tab(tab, [&](int i) { return (uint32_t)phi[i]; }, lo) : 0;
+    const int lo_idx = windowed ? lower_bound16(R.phi + b0, nb, lo) : 0;
     scan_from<G>(S, R, b0, nb, xp, yp, cut, windowed, lo_idx, lo, width, plane, better, take);
 }
 
-// Candidates a[0, na) of one middle hit: extrapolation to each plane of
-// module i, the window's start from the module's bucket table, then the
-// window scan.  Keeps the best (scatter, a, b).
-template <class G, class HS>
-__device__ __forceinline__ void seed_candidate(const DevConfig& C, const Smem& S, const Region<HS>& R,
-                                               int i, int i0, int ni, float4 Cc, float sqrt_cut, int au,
-                                               bool& have, float& best_sc, int& best_a, int& best_b)
+// First index in keys[0, n) whose upper 16 bits are >= v.
+__device__ __forceinline__ int lower_bound_hi16(const uint32_t* keys, int n, uint32_t v)
 {
-    const float4 A = R.coords[au];
-    const uint16_t* tab = module_tab(S, i);
-    const uint16_t* phi = R.phi + i0;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((keys[mid] >> 16) < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kSeedBatch = 1;
+
+// Candidates a[0, na) of one middle hit, processed together: extrapolations
+// to each plane of module i, then the binary searches of their windows in
+// lockstep (independent loads in flight), then the window scans.  Keeps the
+// best (scatter, a, b).
+template <class G, class HS>
+__device__ __forceinline__ void seed_candidates(const DevConfig& C, const Smem& S, const Region<HS>& R,
+                                                int i, int i0, int ni, float4 Cc, float sqrt_cut,
+                                                const int* a, int na, bool& have, float& best_sc,
+                                                int& best_a, int& best_b)
+{
     for (int plane = 0; plane < G::kPlanes; plane++) {
-        float xp, yp;
-        uint32_t lo, width;
-        extrapolate(A, Cc, G::z(C, i, plane), xp, yp);
-        const bool win = window_of(xp, yp, C.S_seed, sqrt_cut, lo, width);
-        const int L = win ? lower_bound_tab(tab, [&](int k) { return (uint32_t)phi[k]; }, lo) : 0;
-        scan_from<G>(
-            S, R, i0, ni, xp, yp, C.S_seed, win, L, lo, width, plane,
-            [&](float sc, int b) {
-                return !have || sc < best_sc || (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
-            },
-            [&](float sc, int b) {
-                have = true;
-                best_sc = sc;
-                best_a = au;
-                best_b = b;
-            });
+        const float zi = G::z(C, i, plane);
+        float xp[kSeedBatch], yp[kSeedBatch];
+        uint32_t lo[kSeedBatch], width[kSeedBatch];
+        int L[kSeedBatch], H[kSeedBatch];
+        bool win[kSeedBatch];
+#pragma unroll
+        for (int u = 0; u < kSeedBatch; u++) {
+            L[u] = 0;
+            H[u] = 0;
+            win[u] = false;
+            if (u < na) {
+                extrapolate(R.coords[a[u]], Cc, zi, xp[u], yp[u]);
+                win[u] = window_of(xp[u], yp[u], C.S_seed, sqrt_cut, lo[u], width[u]);
+                H[u] = win[u] ? ni : 0;
+            }
+        }
+        const uint16_t* phi = R.phi + i0;
+        for (int it = 0; it < 17; it++) {
+            bool active = false;
+#pragma unroll
+            for (int u = 0; u < kSeedBatch; u++) active |= L[u] < H[u];
+            if (!active) break;
+#pragma unroll
+            for (int u = 0; u < kSeedBatch; u++) {
+                if (L[u] < H[u]) {
+                    const int mid = (L[u] + H[u]) >> 1;
+                    if ((uint32_t)phi[mid] < lo[u])
+                        L[u] = mid + 1;
+                    else
+                        H[u] = mid;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSeedBatch; u++) {
+            if (u >= na) continue;
+            const int au = a[u];
+            scan_from<G>(
+                S, R, i0, ni, xp[u], yp[u], C.S_seed, win[u], win[u] ? L[u] : 0, lo[u], width[u], plane,
+                [&](float sc, int b) {
+                    return !have || sc < best_sc ||
+                           (sc == best_sc && (au < best_a || (au == best_a && b < best_b)));
+                },
+                [&](float sc, int b) {
+                    have = true;
+                    best_sc = sc;
+                    best_a = au;
+                    best_b = b;
+                });
+        }
     }
 }
 
@@ -691,12 +706,14 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
     if (nu <= 0 || ni <= 0) return false;
     const uint32_t phc = R.phi[c];
     const float4 Cc = R.coords[c];
-    const int j = lower_bound_tab(outer_tab(S), [&](int k) { return outer[k] >> 16; }, phc);
+    const int j = lower_bound_hi16(outer, nu, phc);
     int up = j, dn = j - 1;
     int found = 0, dK = INT_MAX;
     bool have = false;
     float best_sc = 0.0f;
     int best_a = 0, best_b = 0;
+    int cand[kSeedBatch];
+    int nc = 0;
     for (int visited = 0; visited < nu; visited++) {
         const int iu = up >= nu ? up - nu : up;
         const int id = dn < 0 ? dn + nu : dn;
@@ -716,8 +733,14 @@ __device__ bool seed_for(const DevConfig& C, const Smem& S, const Region<HS>& R,
         if (found >= C.K && d > dK) break;
         found++;
         if (found == C.K) dK = d;
-        seed_candidate<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, a, have, best_sc, best_a, best_b);
+        cand[nc++] = a;
+        if (nc == kSeedBatch) {
+            seed_candidates<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
+            nc = 0;
+        }
     }
+    if (nc > 0)
+        seed_candidates<G>(C, S, R, s + 2, i0, ni, Cc, sqrt_cut, cand, nc, have, best_sc, best_a, best_b);
     if (have) {
         oa = best_a;
         ob = best_b;
@@ -739,7 +762,7 @@ __device__ bool follow_best(const DevConfig& C, const Smem& S, const Region<HS>&
         float xp, yp;
         extrapolate(A, Cc, G::z(C, t, plane), xp, yp);
         scan_window<G>(
-            S, R, b0, nb, module_tab(S, t), xp, yp, C.S_follow, sqrt_cut, plane,
+            S, R, b0, nb, xp, yp, C.S_follow, sqrt_cut, plane,
             [&](float sc, int b) { return !have || sc < best || (sc == best && b < bb); },
             [&](float sc, int b) {
                 have = true;
@@ -863,13 +886,6 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
         }
         if (s + 3 <= M - 1)  // claim words of the target module start empty
             for (int p = S.modoff[s + 3] + tid; p < S.modoff[s + 4]; p += NT) R.claim[p] = ~0ull;
-        // bucket tables of the modules searched in this step: s+2 (seeding;
-        // built in the previous step as its following target) and s+3
-        for (int m = s == 0 ? 2 : 3 + s; m <= min(s + 3, M - 1); m++) {
-            const uint16_t* ph = R.phi + S.modoff[m];
-            build_tab(module_tab(S, m), S.modoff[m + 1] - S.modoff[m],
-                      [&](int i) { return (uint32_t)ph[i]; }, tid, NT);
-        }
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
         uint32_t* outer = list + (c1 - c0);
         for (int base = c0 + (tid & ~31); base < c1; base += NT) {
@@ -894,8 +910,6 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
                 nu += __popc(m);
             }
             if (lane == 0) misc[kNOuter] = nu;
-            __syncwarp();
-            build_tab(outer_tab(S), nu, [&](int i) { return outer[i] >> 16; }, lane, 32);
         }
         __syncthreads();
         const int nl = misc[kList];
@@ -1038,95 +1052,40 @@ __device__ void tracklet_filter(const DevConfig& C, const Region<HS>& R, const S
     __syncthreads();
 }
 
-// Canonical order (smallest input hit index), staging of the hit lists and
-// the least-squares fit of every track on the sorted coordinates.  Each
-// track's linked hit list is walked once, into `pos` at the track's place in
-// found order; ranks then come from a running count of marks over input
-// indices, and the hit writes and fit passes read `pos` (independent loads).
+// Staging of the tracks: each track's linked hit list is walked once, its
+// hit records written in traversal order at its found-order place among the
+// event's staged hits, with its smallest input index.  Ordering and fits are
+// left to the output kernel.
 template <int NT, class HS>
-__device__ void output_stage(const DevConfig& C, int e, int off, int n, const Region<HS>& R,
-                             const Smem& S, const Staging& G, const sbt_tracks& out)
+__device__ void output_stage(int e, int off, const Region<HS>& R, const Smem& S, const Staging& G,
+                             const sbt_tracks& out)
 {
     const int tid = threadIdx.x;
     const int T = S.misc[kNFin];
-    uint16_t* mark = R.mark;
-    uint16_t* pos = R.pos;
-    // found-order starts (fin_start holds them until the canonical starts replace them)
-    {
-        const int chunk = (T + NT - 1) / NT;
-        const int beg = min(T, tid * chunk), end = min(T, beg + chunk);
-        int cnt = 0;
-        for (int k = beg; k < end; k++) cnt += (int)(R.finals[k] >> 16);
-        int total;
-        int st = block_exclusive_scan<NT>(cnt, S.wsum, &total);
-        for (int k = beg; k < end; k++) {
-            R.fin_rank[k] = st;  // found-order start, replaced by the rank below
-            st += (int)(R.finals[k] >> 16);
-        }
-    }
-    __syncthreads();
-    for (int k = tid; k < T; k += NT) {
+    const int chunk = (T + NT - 1) / NT;
+    const int beg = min(T, tid * chunk), end = min(T, beg + chunk);
+    int cnt = 0;
+    for (int k = beg; k < end; k++) cnt += (int)(R.finals[k] >> 16);
+    int H;
+    int u = block_exclusive_scan<NT>(cnt, S.wsum, &H);
+    const int64_t slot0 = (int64_t)off / 3 + e;
+    float4* hits = G.hits + off;
+    for (int k = beg; k < end; k++) {
         const uint32_t v = R.finals[k];
         int q = (int)(v & 0xFFFF);
         const int nh = (int)(v >> 16);
-        const int u = R.fin_rank[k];
         int mn = INT_MAX;
         for (int j = nh - 1; j >= 0; j--) {
-            pos[u + j] = (uint16_t)q;
             const int nq = R.prev[q];
-            const int i = __float_as_int(R.coords[q].w);
+            const float4 c = R.coords[q];
+            hits[u + j] = c;
+            const int i = __float_as_int(c.w);
             mn = i < mn ? i : mn;
             q = nq;
         }
-        mark[mn] = (uint16_t)k;
-    }
-    __syncthreads();
-    // ranks: running count of marks over input indices; a track's found-order
-    // start moves to fin_start[rank]
-    {
-        const int chunk = (n + NT - 1) / NT;
-        const int beg = min(n, tid * chunk), end = min(n, beg + chunk);
-        int cnt = 0;
-        for (int i = beg; i < end; i++) cnt += mark[i] != kNone;
-        int total;
-        int r = block_exclusive_scan<NT>(cnt, S.wsum, &total);
-        for (int i = beg; i < end; i++)
-            if (mark[i] != kNone) {
-                const int k = mark[i];
-                R.fin_start[r] = R.fin_rank[k];
-                R.fin_rank[k] = r++;
-            }
-    }
-    __syncthreads();
-    const int64_t slot0 = (int64_t)off / 3 + e;
-    uint8_t* len = G.len + slot0;
-    for (int k = tid; k < T; k += NT) len[R.fin_rank[k]] = (uint8_t)(R.finals[k] >> 16);
-    __syncthreads();
-    // canonical starts (scan of lengths in rank order); each thread then
-    // handles whole tracks in rank order
-    int H;
-    {
-        const int chunk = (T + NT - 1) / NT;
-        const int beg = min(T, tid * chunk), end = min(T, beg + chunk);
-        int cnt = 0;
-        for (int r = beg; r < end; r++) cnt += len[r];
-        int st = block_exclusive_scan<NT>(cnt, S.wsum, &H);
-        for (int r = beg; r < end; r++) {
-            const int nh = len[r];
-            const int u = R.fin_start[r];
-            for (int j = 0; j < nh; j++) G.hits[(int64_t)off + st + j] = off + __float_as_int(R.coords[pos[u + j]].w);
-            float p[4], chi2;
-            fit_line(
-                nh,
-                [&](int i) {
-                    const float4 c = R.coords[pos[u + i]];
-                    return make_float3(c.x, c.y, c.z);
-                },
-                C.sigma, p, &chi2);
-            G.fit[slot0 + r] = make_float4(p[0], p[1], p[2], p[3]);
-            G.chi2[slot0 + r] = chi2;
-            st += nh;
-        }
+        G.tkey[slot0 + k] = mn;
+        G.tinfo[slot0 + k] = (uint32_t)u | ((uint32_t)nh << 16);
+        u += nh;
     }
     if (tid == 0) {
         G.ev_ntracks[e] = T;
@@ -1161,7 +1120,6 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
     Region<HS> R = region_of<HS>(O, off, W, hb, r, cap);
     for (int m = tid; m <= C.M; m += NT) S.modoff[m] = O.modoff[(int64_t)e * (C.M + 1) + m];
     for (int w = tid; w < (n + 31) / 32; w += NT) S.flag[w] = 0u;
-    for (int p = tid; p < n; p += NT) R.mark[p] = kNone;
     __syncthreads();
     // claim words of the modules that are never a following target
     for (int p = tid; p < S.modoff[min(3, C.M)]; p += NT) R.claim[p] = ~0ull;
@@ -1172,7 +1130,7 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
         return;
     }
     tracklet_filter<NT>(C, R, S);
-    output_stage<NT>(C, e, off, n, R, S, G, out);
+    output_stage<NT>(e, off, R, S, G, out);
     __syncthreads();
 }
 
@@ -1282,58 +1240,161 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
     }
 }
 
-// Consolidation: one warp per event copies the event's staged, already
-// ordered and fitted tracks into the CSR output (coalesced within the warp).
-__global__ void __launch_bounds__(256) k_consolidate(DevConfig C, Inputs in, Staging G,
-                                                      sbt_tracks out)
+// Least-squares fit of a track whose first kFitCache hit records sit in
+// registers (cx, cy, cz) and whose others are read from src; sums in hit
+// order, every operation rounded as in fit_line.
+constexpr int kFitCache = 8;
+
+__device__ __forceinline__ void fit_cached(int n, const float* cx, const float* cy, const float* cz,
+                                           const float4* src, float sigma, float* params, float* chi2)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= in.n_events) return;
-    const int e = warp;
-    const int off = in.offsets[e];
-    const int T = G.ev_ntracks[e];
-    const int H = G.ev_nhits[e];
-    const int tb = G.track_base[e], hbse = G.hit_base[e];
-    if ((int64_t)tb + T > out.cap_tracks || (int64_t)hbse + H > out.cap_hits) return;
-    const int64_t slot0 = (int64_t)off / 3 + e;
-    const uint8_t* len = G.len + slot0;
-    int carry = 0;
-    for (int r0 = 0; r0 < T; r0 += 32) {
-        int r = r0 + lane;
-        int l = r < T ? len[r] : 0;
-        int incl = l;
+    const float nf = (float)n;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += t;
+    for (int i = 0; i < kFitCache; i++)
+        if (i < n) {
+            sx = __fadd_rn(sx, cx[i]);
+            sy = __fadd_rn(sy, cy[i]);
+            sz = __fadd_rn(sz, cz[i]);
         }
-        int start = carry + incl - l;
-        carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (r >= T) continue;
-        const int g = tb + r;
-        out.hit_offsets[g] = hbse + start;
-        float4 p = G.fit[slot0 + r];
-        out.params[4 * (int64_t)g + 0] = p.x;
-        out.params[4 * (int64_t)g + 1] = p.y;
-        out.params[4 * (int64_t)g + 2] = p.z;
-        out.params[4 * (int64_t)g + 3] = p.w;
-        out.chi2[g] = G.chi2[slot0 + r];
-        out.ndof[g] = 2 * l - 4;
+    for (int i = kFitCache; i < n; i++) {
+        const float4 q = src[i];
+        sx = __fadd_rn(sx, q.x);
+        sy = __fadd_rn(sy, q.y);
+        sz = __fadd_rn(sz, q.z);
     }
-    const int32_t* src = G.hits + off;
-    int32_t* dst = out.track_hits + hbse;
-    // four independent loads in flight per lane
-    int j = lane;
-    for (; j + 96 < H; j += 128) {
-        const int32_t a = src[j], b = src[j + 32], c = src[j + 64], d = src[j + 96];
-        dst[j] = a;
-        dst[j + 32] = b;
-        dst[j + 64] = c;
-        dst[j + 96] = d;
+    const float xm = __fdiv_rn(sx, nf), ym = __fdiv_rn(sy, nf), zm = __fdiv_rn(sz, nf);
+    float szz = 0.0f, szx = 0.0f, szy = 0.0f;
+    auto moments = [&](float x, float y, float z) {
+        const float dz = __fsub_rn(z, zm);
+        szz = __fadd_rn(szz, __fmul_rn(dz, dz));
+        szx = __fadd_rn(szx, __fmul_rn(dz, __fsub_rn(x, xm)));
+        szy = __fadd_rn(szy, __fmul_rn(dz, __fsub_rn(y, ym)));
+    };
+#pragma unroll
+    for (int i = 0; i < kFitCache; i++)
+        if (i < n) moments(cx[i], cy[i], cz[i]);
+    for (int i = kFitCache; i < n; i++) {
+        const float4 q = src[i];
+        moments(q.x, q.y, q.z);
     }
-    for (; j < H; j += 32) dst[j] = src[j];
+    const float tx = __fdiv_rn(szx, szz);
+    const float ty = __fdiv_rn(szy, szz);
+    float s = 0.0f;
+    auto resid = [&](float x, float y, float z) {
+        const float dz = __fsub_rn(z, zm);
+        const float rx = __fsub_rn(__fsub_rn(x, xm), __fmul_rn(tx, dz));
+        const float ry = __fsub_rn(__fsub_rn(y, ym), __fmul_rn(ty, dz));
+        s = __fadd_rn(s, __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)));
+    };
+#pragma unroll
+    for (int i = 0; i < kFitCache; i++)
+        if (i < n) resid(cx[i], cy[i], cz[i]);
+    for (int i = kFitCache; i < n; i++) {
+        const float4 q = src[i];
+        resid(q.x, q.y, q.z);
+    }
+    params[0] = __fsub_rn(xm, __fmul_rn(tx, zm));
+    params[1] = __fsub_rn(ym, __fmul_rn(ty, zm));
+    params[2] = tx;
+    params[3] = ty;
+    *chi2 = __fdiv_rn(s, __fmul_rn(sigma, sigma));
 }
+
+// Output (section "Results", data consolidation), one block per event,
+// straight into the CSR arrays: canonical order of the event's tracks by
+// smallest input hit index, their hit lists (batch input indices, traversal
+// order) and the least-squares fit of every track on its staged hit records
+// (coordinates as the hit storage keeps them).  A track's rank is the number
+// of tracks with a smaller smallest index: one bit per input index marks the
+// tracks' smallest indices (shared memory), and a prefix of the words' bit
+// counts gives every rank.
+constexpr int kOutputThreads = 256;
+
+__global__ void __launch_bounds__(kOutputThreads) k_output(DevConfig C, Inputs in, Staging G,
+                                                          sbt_tracks out)
+{
+    constexpr int NT = kOutputThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nwmax = (C.nmax + 31) / 32;
+    uint32_t* bits = (uint32_t*)smem_raw;  // [nwmax]
+    int* wpre = (int*)(bits + nwmax);      // [nwmax]
+    __shared__ int wsum[40];
+    const int e = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int T = G.ev_ntracks[e];
+    if (T == 0) return;
+    const int H = G.ev_nhits[e];
+    const int tb = G.track_base[e], hbase = G.hit_base[e];
+    if ((int64_t)tb + T > out.cap_tracks || (int64_t)hbase + H > out.cap_hits) return;
+    const int off = in.offsets[e];
+    const int n = in.offsets[e + 1] - off;
+    const int64_t slot0 = (int64_t)off / 3 + e;
+    const int nw = (n + 31) / 32;
+    for (int w = tid; w < nw; w += NT) bits[w] = 0u;
+    __syncthreads();
+    for (int k = tid; k < T; k += NT) {
+        const int mn = G.tkey[slot0 + k];
+        atomicOr(&bits[mn >> 5], 1u << (mn & 31));
+    }
+    __syncthreads();
+    {
+        const int wc = (nw + NT - 1) / NT;
+        const int wb = min(nw, tid * wc), we = min(nw, wb + wc);
+        int c = 0;
+        for (int w = wb; w < we; w++) c += __popc(bits[w]);
+        int tot;
+        int st = block_exclusive_scan<NT>(c, wsum, &tot);
+        for (int w = wb; w < we; w++) {
+            wpre[w] = st;
+            st += __popc(bits[w]);
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < T; k += NT) {
+        const int mn = G.tkey[slot0 + k];
+        const int r = wpre[mn >> 5] + __popc(bits[mn >> 5] & ((1u << (mn & 31)) - 1u));
+        G.rinfo[slot0 + r] = G.tinfo[slot0 + k];
+    }
+    __syncthreads();
+    // canonical starts: each thread takes a contiguous run of ranks
+    const int chunk = (T + NT - 1) / NT;
+    const int beg = min(T, tid * chunk), end = min(T, beg + chunk);
+    int c = 0;
+    for (int r = beg; r < end; r++) c += (int)(G.rinfo[slot0 + r] >> 16);
+    int Ht;
+    int cs = block_exclusive_scan<NT>(c, wsum, &Ht);
+    for (int r = beg; r < end; r++) {
+        const uint32_t ri = G.rinfo[slot0 + r];
+        const int nh = (int)(ri >> 16);
+        const float4* src = G.hits + off + (ri & 0xFFFFu);
+        const int64_t g = (int64_t)tb + r;
+        const int64_t h0 = (int64_t)hbase + cs;
+        out.hit_offsets[g] = (int32_t)h0;
+        float cx[kFitCache], cy[kFitCache], cz[kFitCache];
+#pragma unroll
+        for (int i = 0; i < kFitCache; i++)
+            if (i < nh) {
+                const float4 q = src[i];
+                cx[i] = q.x;
+                cy[i] = q.y;
+                cz[i] = q.z;
+                out.track_hits[h0 + i] = off + __float_as_int(q.w);
+            }
+        for (int i = kFitCache; i < nh; i++) out.track_hits[h0 + i] = off + __float_as_int(src[i].w);
+        float p[4], chi2;
+        fit_cached(nh, cx, cy, cz, src, C.sigma, p, &chi2);
+        out.params[4 * g + 0] = p[0];
+        out.params[4 * g + 1] = p[1];
+        out.params[4 * g + 2] = p[2];
+        out.params[4 * g + 3] = p[3];
+        out.chi2[g] = chi2;
+        out.ndof[g] = 2 * nh - 4;
+        cs += nh;
+    }
+}
+
+size_t output_smem_bytes(int nmax) { return 8 * (size_t)((nmax + 31) / 32); }
 
 // Chunked host pipeline: adds the totals of the earlier chunks to one chunk's
 // CSR offsets (track_offsets [n_events + 1], hit_offsets [counts[0] + 1]) and
@@ -1499,13 +1560,13 @@ cudaError_t launch_scan(const Inputs& in, const Staging& S, const sbt_tracks& ou
     return cudaGetLastError();
 }
 
-cudaError_t launch_consolidate(const DevConfig& C, const Inputs& in, const Staging& S,
-                               const sbt_tracks& out, cudaStream_t stream)
+cudaError_t launch_output(const DevConfig& C, const Inputs& in, const Staging& S,
+                          const sbt_tracks& out, cudaStream_t stream)
 {
-    if (in.n_events > 0) {
-        int blocks = (in.n_events + 7) / 8;
-        k_consolidate<<<blocks, 256, 0, stream>>>(C, in, S, out);
-    }
+    const size_t sm = output_smem_bytes(C.nmax);
+    cudaError_t err = cudaFuncSetAttribute(k_output, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    if (in.n_events > 0) k_output<<<in.n_events, kOutputThreads, sm, stream>>>(C, in, S, out);
     return cudaGetLastError();
 }
 
@@ -1513,7 +1574,7 @@ cudaError_t launch_finish(const DevConfig& C, const Inputs& in, const Staging& S
                           const sbt_tracks& out, cudaStream_t stream)
 {
     cudaError_t e = launch_scan(in, S, out, stream);
-    if (e == cudaSuccess) e = launch_consolidate(C, in, S, out, stream);
+    if (e == cudaSuccess) e = launch_output(C, in, S, out, stream);
     return e;
 }
 
