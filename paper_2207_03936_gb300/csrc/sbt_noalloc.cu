@@ -66,7 +66,7 @@ constexpr Layout make_layout()
 
 constexpr Layout kLayout = make_layout();
 
-// The workspace (about 45 MB).  In host code this name is only a host-side
+// The workspace (about 46 MB).  In host code this name is only a host-side
 // stand-in: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_workspace[kLayout.total];
 
