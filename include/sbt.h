@@ -185,14 +185,27 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
                                 void* stream);
 
 /*
- * Times the batched kernel for each block size in {64, 128, 256} on the given
- * events (device inputs as in sbt_reconstruct) and keeps the fastest in the
- * handle.  Results do not depend on the choice.  Synchronous.  *chosen
- * (host, may be NULL) receives the block size.
+ * Times the batched search kernel on the given events (device inputs as in
+ * sbt_reconstruct) for each block size in {64, 128, 256} and, for each, the
+ * occupancy limit of resident blocks per SM, three quarters and half of it,
+ * and keeps the fastest shape in the handle for the batched and host entry
+ * points.  Results do not depend on the choice.  Synchronous.  *chosen and
+ * *chosen_blocks_per_sm (host, each may be NULL) receive the shape.
  */
 sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const float* z,
                         const int32_t* module, const int32_t* event_offsets, int32_t n_events,
-                        int32_t n_hits, int32_t* chosen, void* stream);
+                        int32_t n_hits, int32_t* chosen, int32_t* chosen_blocks_per_sm, void* stream);
+
+/* The handle's tuned launch shape (host outputs): block size and resident
+ * blocks per SM of the persistent launch; 0 and 0 before sbt_autotune. */
+sbt_status sbt_tuned_shape(const sbt_handle* h, int32_t* threads, int32_t* blocks_per_sm);
+
+/* Sets the launch shape of the persistent launch as sbt_autotune would (for
+ * example the shape tuned on another handle for the same workload): threads
+ * 64, 128 or 256 (a nonzero threads_per_block of the configuration still
+ * takes precedence), blocks_per_sm > 0 caps the resident blocks per SM
+ * (0 = occupancy limit).  SBT_ERR_ARG otherwise. */
+sbt_status sbt_set_launch_shape(sbt_handle* h, int32_t threads, int32_t blocks_per_sm);
 
 /*
  * Differentiation of the consolidation fit with respect to per-module
@@ -345,11 +358,18 @@ sbt_status sbt_server_drain(sbt_server* s, int64_t* ids, int32_t* status, double
 /* Frees the host memory of a polled result. */
 sbt_status sbt_server_release(sbt_server* s, int64_t request_id);
 
-/* stats (host, 8 doubles): completed, submitted, batches launched, mean
+/* stats (host, 14 doubles): completed, submitted, batches launched, mean
  * events per batch, peak device bytes in flight, failed batches, the largest
  * delay (seconds) of the latest open-loop schedule's generator behind that
- * schedule, and the launcher thread's total time (seconds) spent enqueueing
- * batches (copies, kernels, downloads). */
+ * schedule, the launcher thread's total time (seconds) spent enqueueing
+ * batches (copies, kernels, downloads); then, summed over the batches that
+ * finished, the milliseconds spent in uploads, in reconstruction kernels and
+ * in downloads (CUDA events on each slot's stream) and from enqueueing to
+ * harvesting (host clock), and the number of batches these sums cover; last,
+ * the device and pinned host allocations the servers of this process made
+ * since this one was created (slots and result blocks grow to the largest
+ * batch they meet and then allocate nothing; buffers they outgrow are kept
+ * until sbt_server_destroy, since freeing would stall the device). */
 sbt_status sbt_server_stats(sbt_server* s, double* stats);
 
 /* Makes the next launched batch fail on the host side (test hook for the

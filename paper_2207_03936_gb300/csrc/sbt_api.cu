@@ -33,28 +33,32 @@ constexpr int kWeightedChunks = sizeof(kChunkWeights) / sizeof(kChunkWeights[0])
 struct Arena {
     void* base = nullptr;
     size_t bytes = 0;
+    bool defer = false;          // keep outgrown allocations until release()
+    std::vector<void*> retired;
     // Grows geometrically: freeing device memory synchronises the device, so
     // workspaces must not be reallocated for every slightly larger batch.
     cudaError_t reserve(size_t need)
     {
         if (need <= bytes) return cudaSuccess;
         if (bytes) need = std::max(need, bytes + bytes / 2);
-        if (base) {
+        if (base && !defer) {
             cudaError_t e = cudaFree(base);
             base = nullptr;
             bytes = 0;
             if (e != cudaSuccess) return e;
         }
-        cudaError_t e = cudaMalloc(&base, need);
-        if (e != cudaSuccess) {
-            base = nullptr;
-            return e;
-        }
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) return e;
+        if (base) retired.push_back(base);
+        base = p;
         bytes = need;
         return cudaSuccess;
     }
     void release()
     {
+        for (void* p : retired) cudaFree(p);
+        retired.clear();
         if (base) cudaFree(base);
         base = nullptr;
         bytes = 0;
@@ -141,6 +145,7 @@ struct sbt_handle {
     std::string err;
     Arena plain_arena, pers_arena, stage_arena, host_arena, misc_arena, sorted_arena;
     int tuned_threads = 0;
+    int tuned_blocks_per_sm = 0;  // resident blocks per SM of the persistent launch (0: occupancy limit)
     cudaStream_t cap_stream = nullptr;
     cudaStream_t copy_in = nullptr, copy_out = nullptr, sort_stream = nullptr;
     int32_t* host_counts = nullptr;  // pinned, 4 per chunk of the host pipeline
@@ -231,9 +236,15 @@ sbt_status ensure_staging(sbt_handle* h, int64_t n_hits, int64_t n_events, Stagi
     return SBT_OK;
 }
 
-int persistent_blocks(sbt_handle* h, int threads)
+// Grid of the persistent launch: resident blocks per SM (the autotuned count
+// when it was tuned for this block size, else the occupancy limit) times SMs.
+int persistent_blocks(sbt_handle* h, int threads, int per_sm_wanted = 0)
 {
     int per_sm = persistent_blocks_per_sm(h->C, threads);
+    if (per_sm_wanted > 0)
+        per_sm = std::min(per_sm, per_sm_wanted);
+    else if (threads == h->tuned_threads && h->tuned_blocks_per_sm > 0)
+        per_sm = std::min(per_sm, h->tuned_blocks_per_sm);
     return std::max(per_sm, 1) * h->sm_count;
 }
 
@@ -273,6 +284,13 @@ int handle_plain_threads(const sbt_handle* h) { return default_threads(h, false)
 void handle_set_error(sbt_handle* h, const std::string& msg) { h->err = msg; }
 
 void handle_set_launches(sbt_handle* h, int launches) { h->launches_last = launches; }
+
+void handle_defer_frees(sbt_handle* h)
+{
+    for (Arena* a : {&h->plain_arena, &h->pers_arena, &h->stage_arena, &h->host_arena, &h->misc_arena,
+                     &h->sorted_arena})
+        a->defer = true;
+}
 
 }  // namespace sbt
 
@@ -683,7 +701,7 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
 
 sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const float* z,
                         const int32_t* module, const int32_t* event_offsets, int32_t n_events,
-                        int32_t n_hits, int32_t* chosen, void* stream)
+                        int32_t n_hits, int32_t* chosen, int32_t* chosen_blocks_per_sm, void* stream)
 {
     sbt_status st = check_inputs(h, x, y, z, module, event_offsets, n_events, n_hits, nullptr);
     if (st != SBT_OK) return st;
@@ -705,42 +723,79 @@ sbt_status sbt_autotune(sbt_handle* h, const float* x, const float* y, const flo
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     float best_ms = 1e30f;
-    int best = 128;
+    int best = 128, best_per_sm = 0;
+    // block sizes, and for each the occupancy limit of resident blocks per SM
+    // and three quarters and half of it (the search waits on load latency:
+    // more resident events hide more of it, but also share L1 and L2)
     const int cands[3] = {64, 128, 256};
     for (int threads : cands) {
-        const int blocks = persistent_blocks(h, threads);
-        Work W;
-        if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) break;
-        float tot = 0.0f;
-        for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
-            e = cudaMemsetAsync(S.queue, 0, 16, s);
-            if (e == cudaSuccess) e = cudaEventRecord(a, s);
-            if (e == cudaSuccess)
-                e = launch_persistent(h->C, in, O, W, S, scratch_out, threads,
-                                      std::min(blocks, std::max(n_events, 1)), s);
-            if (e == cudaSuccess) e = cudaEventRecord(b, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(b);
-            float ms = 0.0f;
-            if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-            if (rep > 0) tot += ms;  // first repetition is warm-up
+        const int limit = std::max(persistent_blocks_per_sm(h->C, threads), 1);
+        int per_sms[3] = {limit, std::max(1, (3 * limit) / 4), std::max(1, limit / 2)};
+        for (int ci = 0; ci < 3 && e == cudaSuccess && st == SBT_OK; ci++) {
+            const int per_sm = per_sms[ci];
+            if (ci > 0 && per_sm == per_sms[ci - 1]) continue;
+            const int blocks = persistent_blocks(h, threads, per_sm);
+            Work W;
+            if ((st = ensure_persistent(h, blocks, &W)) != SBT_OK) break;
+            float tot = 0.0f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+                e = cudaMemsetAsync(S.queue, 0, 16, s);
+                if (e == cudaSuccess) e = cudaEventRecord(a, s);
+                if (e == cudaSuccess)
+                    e = launch_persistent(h->C, in, O, W, S, scratch_out, threads,
+                                          std::min(blocks, std::max(n_events, 1)), s);
+                if (e == cudaSuccess) e = cudaEventRecord(b, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float ms = 0.0f;
+                if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) tot += ms;  // first repetition is warm-up
+            }
+            if (e == cudaSuccess && tot < best_ms) {
+                best_ms = tot;
+                best = threads;
+                best_per_sm = per_sm;
+            }
         }
-        if (e != cudaSuccess) break;
-        if (tot < best_ms) {
-            best_ms = tot;
-            best = threads;
-        }
+        if (e != cudaSuccess || st != SBT_OK) break;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st != SBT_OK) return st;
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
     h->tuned_threads = best;
+    h->tuned_blocks_per_sm = best_per_sm;
     if (chosen) *chosen = best;
+    if (chosen_blocks_per_sm) *chosen_blocks_per_sm = best_per_sm;
     if (h->exec) {  // the workspace may have moved
         cudaGraphExecDestroy(h->exec);
         h->exec = nullptr;
         h->have_key = false;
     }
+    return SBT_OK;
+}
+
+/* Sets the launch shape of the persistent search (as sbt_autotune would). */
+sbt_status sbt_set_launch_shape(sbt_handle* h, int32_t threads, int32_t blocks_per_sm)
+{
+    if (!h) return SBT_ERR_ARG;
+    if ((threads != 64 && threads != 128 && threads != 256) || blocks_per_sm < 0)
+        return fail(h, SBT_ERR_ARG, "threads must be 64, 128 or 256 and blocks_per_sm >= 0");
+    h->tuned_threads = threads;
+    h->tuned_blocks_per_sm = blocks_per_sm;
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+        h->have_key = false;
+    }
+    return SBT_OK;
+}
+
+/* Tuned launch shape of the handle (0, 0 before sbt_autotune). */
+sbt_status sbt_tuned_shape(const sbt_handle* h, int32_t* threads, int32_t* blocks_per_sm)
+{
+    if (!h || !threads || !blocks_per_sm) return SBT_ERR_ARG;
+    *threads = h->tuned_threads;
+    *blocks_per_sm = h->tuned_blocks_per_sm;
     return SBT_OK;
 }
 

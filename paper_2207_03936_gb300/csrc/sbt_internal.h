@@ -147,5 +147,9 @@ const DevConfig& handle_device_config(const sbt_handle* h);
 int handle_plain_threads(const sbt_handle* h);
 void handle_set_error(sbt_handle* h, const std::string& msg);
 void handle_set_launches(sbt_handle* h, int launches);
+// Workspaces the handle outgrows are kept until sbt_destroy instead of freed
+// (cudaFree synchronises the device); for handles whose work overlaps other
+// streams' work, such as the serving slots.
+void handle_defer_frees(sbt_handle* h);
 
 }  // namespace sbt

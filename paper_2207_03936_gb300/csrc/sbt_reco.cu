@@ -1136,9 +1136,14 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
 
 // ------------------------------------------------------------- kernels ---
 
+// Residency of the search: the kernel waits on load latency, so throughput
+// follows the number of resident events; the compiler is asked for a
+// register count that lets 2048 threads (32 blocks of 64) share an SM.
+constexpr int kSearchThreadsPerSM = 2048;
+
 // One block per event.
 template <int NT, class HS, class GEO>
-__global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sorted O, Work W,
+__global__ void __launch_bounds__(NT, kSearchThreadsPerSM / NT) k_search_plain(DevConfig C, Inputs in, Sorted O, Work W,
                                                       Staging G, sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1153,7 +1158,7 @@ __global__ void __launch_bounds__(NT) k_search_plain(DevConfig C, Inputs in, Sor
 // alternating from both ends of G.order (largest first), and reuses its own
 // scratch region.
 template <int NT, class HS, class GEO>
-__global__ void __launch_bounds__(NT) k_search_persistent(DevConfig C, Inputs in, Sorted O, Work W,
+__global__ void __launch_bounds__(NT, kSearchThreadsPerSM / NT) k_search_persistent(DevConfig C, Inputs in, Sorted O, Work W,
                                                            Staging G, sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1243,7 +1248,7 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
 // Least-squares fit of a track whose first kFitCache hit records sit in
 // registers (cx, cy, cz) and whose others are read from src; sums in hit
 // order, every operation rounded as in fit_line.
-constexpr int kFitCache = 8;
+constexpr int kFitCache = 4;
 
 __device__ __forceinline__ void fit_cached(int n, const float* cx, const float* cy, const float* cz,
                                            const float4* src, float sigma, float* params, float* chi2)

@@ -37,23 +37,37 @@ double now_s()
     return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
 }
 
+// Allocations made by the servers of this process (device and pinned host),
+// for the stats: in steady state a server allocates nothing.
+std::atomic<int64_t> g_allocs{0};
+
+// Device and pinned host buffers of the slots and result blocks.  They grow
+// with headroom (a quarter above the request, at least half again the old
+// size) and keep the buffers they outgrow until release(): cudaFree and
+// cudaFreeHost synchronise the device, which would stall every other slot's
+// work in flight.
 template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    std::vector<T*> retired;
     cudaError_t reserve(size_t want)
     {
         if (want <= n) return cudaSuccess;
-        if (n) want = std::max(want, n + n / 2);  // grow geometrically: frees synchronise
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-        cudaError_t e = cudaMalloc(&p, sizeof(T) * std::max<size_t>(want, 1));
-        if (e == cudaSuccess) n = want;
-        return e;
+        want = std::max(want + want / 4, n + n / 2);
+        T* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(want, 1));
+        if (e != cudaSuccess) return e;
+        g_allocs.fetch_add(1);
+        if (p) retired.push_back(p);
+        p = q;
+        n = want;
+        return cudaSuccess;
     }
     void release()
     {
+        for (T* q : retired) cudaFree(q);
+        retired.clear();
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
@@ -64,19 +78,24 @@ template <class T>
 struct HostBuf {
     T* p = nullptr;
     size_t n = 0;
+    std::vector<T*> retired;
     cudaError_t reserve(size_t want)
     {
         if (want <= n) return cudaSuccess;
-        if (n) want = std::max(want, n + n / 2);
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        n = 0;
-        cudaError_t e = cudaMallocHost(&p, sizeof(T) * std::max<size_t>(want, 1));
-        if (e == cudaSuccess) n = want;
-        return e;
+        want = std::max(want + want / 4, n + n / 2);
+        T* q = nullptr;
+        cudaError_t e = cudaMallocHost(&q, sizeof(T) * std::max<size_t>(want, 1));
+        if (e != cudaSuccess) return e;
+        g_allocs.fetch_add(1);
+        if (p) retired.push_back(p);
+        p = q;
+        n = want;
+        return cudaSuccess;
     }
     void release()
     {
+        for (T* q : retired) cudaFreeHost(q);
+        retired.clear();
         if (p) cudaFreeHost(p);
         p = nullptr;
         n = 0;
@@ -102,6 +121,7 @@ struct PinnedBatch {
         if (cudaMallocHost(&x, nb) != cudaSuccess || cudaMallocHost(&y, nb) != cudaSuccess ||
             cudaMallocHost(&z, nb) != cudaSuccess || cudaMallocHost(&m, nb) != cudaSuccess)
             return false;
+        g_allocs.fetch_add(1);
         cap = std::max<size_t>(hits, 1);
         return true;
     }
@@ -156,6 +176,9 @@ struct Slot {
     sbt_handle* h = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t t_up = nullptr, t_kern = nullptr, t_down = nullptr;  // timing: before uploads,
+                                                                     // kernels, downloads
+    double t_enqueued = 0.0;  // host clock when the batch was handed to the slot
     std::atomic<bool> busy{false};
     bool failed = false;
     int64_t bytes = 0;
@@ -197,7 +220,11 @@ struct sbt_server {
     int64_t in_flight_bytes = 0;
     double st_completed = 0, st_submitted = 0, st_batches = 0, st_events_batched = 0,
            st_peak_bytes = 0, st_failed = 0, st_feed_lag = 0;
+    // per-batch time sums (ms): uploads, kernels, downloads on the slot's
+    // stream (CUDA events), and enqueue to harvest on the host clock
+    double st_up_ms = 0, st_kern_ms = 0, st_down_ms = 0, st_wall_ms = 0, st_timed = 0;
     std::atomic<double> st_launch_s{0.0};  // launcher time spent enqueueing batches
+    int64_t allocs0 = 0;                    // g_allocs when the server was created
     std::thread launcher, harvester, feeder;
 };
 
@@ -255,6 +282,7 @@ bool launch_batch(Slot& sl)
     }
     sl.hoff.p[E] = o;
     cudaStream_t s = sl.stream;
+    need(cudaEventRecord(sl.t_up, s));
     if (H) {
         need(cudaMemcpyAsync(sl.dx.p, direct ? sl.reqs[0].x : sl.hx.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
         need(cudaMemcpyAsync(sl.dy.p, direct ? sl.reqs[0].y : sl.hy.p, 4 * (size_t)H, cudaMemcpyHostToDevice, s));
@@ -274,8 +302,10 @@ bool launch_batch(Slot& sl)
     out.counts = sl.dcounts.p;
     out.cap_tracks = (int32_t)capT;
     out.cap_hits = (int32_t)capH;
+    need(cudaEventRecord(sl.t_kern, s));
     if (sbt_reconstruct(sl.h, sl.dx.p, sl.dy.p, sl.dz.p, sl.dm.p, sl.doff.p, E, H, &out, s) != SBT_OK)
         return false;
+    need(cudaEventRecord(sl.t_down, s));
     need(cudaMemcpyAsync(B.to.p, sl.dto.p, 4 * (size_t)(E + 1), cudaMemcpyDeviceToHost, s));
     need(cudaMemcpyAsync(B.stat.p, sl.dstat.p, 4 * (size_t)E, cudaMemcpyDeviceToHost, s));
     need(cudaMemcpyAsync(B.ho.p, sl.dho.p, 4 * (capT + 1), cudaMemcpyDeviceToHost, s));
@@ -327,8 +357,14 @@ void launcher_loop(sbt_server* S)
                 S->all_blocks.push_back(std::make_unique<ResultBlock>());
                 block = S->all_blocks.back().get();
             } else {
-                block = S->free_blocks.back();
-                S->free_blocks.pop_back();
+                // the free block whose track-hit buffer is largest: blocks that
+                // already hold a batch of this size are not grown again
+                auto best = std::max_element(S->free_blocks.begin(), S->free_blocks.end(),
+                                             [](const ResultBlock* a, const ResultBlock* b) {
+                                                 return a->th.n < b->th.n;
+                                             });
+                block = *best;
+                S->free_blocks.erase(best);
             }
         }
         Slot& sl = *free_slot;
@@ -337,6 +373,7 @@ void launcher_loop(sbt_server* S)
         sl.block = block;
         sl.failed = false;
         const double tl = now_s();
+        sl.t_enqueued = tl;
         if (S->inject.exchange(false)) {
             sl.failed = true;  // host-side failure: nothing was enqueued
         } else if (!launch_batch(sl)) {
@@ -353,6 +390,10 @@ void launcher_loop(sbt_server* S)
 void harvest(sbt_server* S, Slot& sl)
 {
     const double t_done = now_s();
+    float up = 0.0f, kern = 0.0f, down = 0.0f;
+    const bool timed = !sl.failed && cudaEventElapsedTime(&up, sl.t_up, sl.t_kern) == cudaSuccess &&
+                       cudaEventElapsedTime(&kern, sl.t_kern, sl.t_down) == cudaSuccess &&
+                       cudaEventElapsedTime(&down, sl.t_down, sl.done) == cudaSuccess;
     std::vector<Finished> out(sl.reqs.size());
     ResultBlock* B = sl.block;
     for (size_t k = 0; k < sl.reqs.size(); k++) {
@@ -380,6 +421,13 @@ void harvest(sbt_server* S, Slot& sl)
         }
         for (auto& f : out) S->finished.push_back(f);
         S->st_completed += (double)out.size();
+        if (timed) {
+            S->st_up_ms += up;
+            S->st_kern_ms += kern;
+            S->st_down_ms += down;
+            S->st_wall_ms += (t_done - sl.t_enqueued) * 1e3;
+            S->st_timed += 1;
+        }
         S->in_flight_bytes -= sl.bytes;
     }
     sl.block = nullptr;
@@ -449,7 +497,10 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
             break;
         }
         e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl->done);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl->t_up);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl->t_kern);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl->t_down);
         S->slots.push_back(std::move(sl));
     }
     if (e != cudaSuccess) {
@@ -457,10 +508,15 @@ sbt_status sbt_server_create(sbt_handle* h, int64_t memory_budget_bytes, int32_t
             if (sl->h) sbt_destroy(sl->h);
             if (sl->stream) cudaStreamDestroy(sl->stream);
             if (sl->done) cudaEventDestroy(sl->done);
+            if (sl->t_up) cudaEventDestroy(sl->t_up);
+            if (sl->t_kern) cudaEventDestroy(sl->t_kern);
+            if (sl->t_down) cudaEventDestroy(sl->t_down);
         }
         delete S;
         return SBT_ERR_CUDA;
     }
+    for (auto& sl : S->slots) sbt::handle_defer_frees(sl->h);
+    S->allocs0 = g_allocs.load();
     S->launcher = std::thread(launcher_loop, S);
     S->harvester = std::thread(harvester_loop, S);
     *out = S;
@@ -696,6 +752,12 @@ sbt_status sbt_server_stats(sbt_server* S, double* stats)
     stats[5] = S->st_failed;
     stats[6] = S->st_feed_lag;
     stats[7] = S->st_launch_s.load(std::memory_order_relaxed);
+    stats[8] = S->st_up_ms;
+    stats[9] = S->st_kern_ms;
+    stats[10] = S->st_down_ms;
+    stats[11] = S->st_wall_ms;
+    stats[12] = S->st_timed;
+    stats[13] = (double)(g_allocs.load() - S->allocs0);
     return SBT_OK;
 }
 
@@ -726,6 +788,9 @@ sbt_status sbt_server_destroy(sbt_server* S)
         sl.dchi2.release(); sl.dndof.release(); sl.dstat.release(); sl.dcounts.release();
         sl.hx.release(); sl.hy.release(); sl.hz.release(); sl.hm.release(); sl.hoff.release();
         cudaEventDestroy(sl.done);
+        cudaEventDestroy(sl.t_up);
+        cudaEventDestroy(sl.t_kern);
+        cudaEventDestroy(sl.t_down);
         cudaStreamDestroy(sl.stream);
         sbt_destroy(sl.h);
     }

@@ -76,7 +76,9 @@ def lib() -> ctypes.CDLL:
             "sbt_reconstruct": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
             "sbt_reconstruct_batched": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
             "sbt_reconstruct_host": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
-            "sbt_autotune": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
+            "sbt_autotune": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P, _P]),
+            "sbt_tuned_shape": (_I32, [_P, _P, _P]),
+            "sbt_set_launch_shape": (_I32, [_P, _I32, _I32]),
             "sbt_fit_adjoint": (_I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _I32, _P, _P, _P, _P, _P]),
             "sbt_debug_sort": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P]),
             "sbt_debug_phi16": (_I32, [_P, _P, _I32, _P, _P]),
@@ -276,17 +278,30 @@ def sbt_reconstruct_noalloc(h: Handle, x, y, z, module, event_offsets, out: Trac
     return _reco(f, h, x, y, z, module, event_offsets, out, stream)
 
 
-def sbt_autotune(h: Handle, x, y, z, module, event_offsets, stream=None) -> int:
+def sbt_autotune(h: Handle, x, y, z, module, event_offsets, stream=None) -> tuple[int, int]:
+    """Tunes the persistent launch on these events: (block size, resident blocks per SM)."""
     px, py, pz, pm, po, E, H = _inputs(x, y, z, module, event_offsets)
-    chosen = ctypes.c_int32()
-    _check(lib().sbt_autotune(h.h, px, py, pz, pm, po, E, H, ctypes.byref(chosen), _stream(stream)),
-           h.h)
-    return int(chosen.value)
+    chosen, per_sm = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sbt_autotune(h.h, px, py, pz, pm, po, E, H, ctypes.byref(chosen), ctypes.byref(per_sm),
+                              _stream(stream)), h.h)
+    return int(chosen.value), int(per_sm.value)
+
+
+def sbt_set_launch_shape(h: Handle, threads: int, blocks_per_sm: int):
+    """Gives the handle a launch shape, e.g. one tuned on another handle."""
+    _check(lib().sbt_set_launch_shape(h.h, int(threads), int(blocks_per_sm)), h.h)
+
+
+def sbt_tuned_shape(h: Handle) -> tuple[int, int]:
+    """(block size, resident blocks per SM) chosen by sbt_autotune; (0, 0) before it."""
+    t, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sbt_tuned_shape(h.h, ctypes.byref(t), ctypes.byref(b)), h.h)
+    return int(t.value), int(b.value)
 
 
 def sbt_profile_batched(h: Handle, x, y, z, module, event_offsets, out: TrackOutput, reps=3,
                         stream=None):
-    """Mean ms per launch of (ordering, sort, persistent search, scan, consolidation)."""
+    """Mean ms per launch of (ordering, sort, persistent search, scan, output)."""
     px, py, pz, pm, po, E, H = _inputs(x, y, z, module, event_offsets)
     ms = (ctypes.c_float * 5)()
     oc = out.c_struct()
@@ -460,11 +475,12 @@ class Server:
         return ids[:k], st[:k], lat[:k]
 
     def stats(self) -> dict:
-        v = (ctypes.c_double * 8)()
+        v = (ctypes.c_double * 14)()
         _check(self.L.sbt_server_stats(self.s, v))
         return {"completed": v[0], "submitted": v[1], "batches": v[2], "mean_batch_events": v[3],
                 "peak_bytes": v[4], "failed_batches": v[5], "feed_lag_s": v[6],
-                "launch_busy_s": v[7]}
+                "launch_busy_s": v[7], "upload_ms": v[8], "kernel_ms": v[9], "download_ms": v[10],
+                "batch_wall_ms": v[11], "timed_batches": v[12], "allocations": v[13]}
 
     def inject_failure(self):
         _check(self.L.sbt_server_inject_failure(self.s))

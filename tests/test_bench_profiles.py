@@ -1,7 +1,8 @@
 """Host logic of the bench line's profile-derived fields (no GPU): the pinned
-ncu counters are used only for the code they were taken on and only for the
-batch they were taken on, and the issue roofline is the captured warp
-instructions over the live kernel time against 4 schedulers per SM."""
+ncu counters are used only for the code they were taken on, scaled per hit
+from the captured batch to the measured one, and the issue roofline is the
+scaled warp instructions over the live kernel time against 4 schedulers per
+SM; without counters the roofline falls back to the HBM fraction."""
 import json
 import os
 import sys
@@ -39,10 +40,10 @@ def test_digest_ignores_comments_and_whitespace(tmp_path):
     assert bench.code_digest(str(a)) != bench.code_digest(str(c))
 
 
-def test_counters_only_for_the_captured_code_and_batch(fake_root):
+def test_counters_only_for_the_captured_code_scaled_per_hit(fake_root):
     assert bench.profiled_traffic("k<64>", 1000) == 400
     assert bench.profiled_traffic("k<128>", 1000) is None      # another block size
-    assert bench.profiled_traffic("k<64>", 999) is None        # another batch
+    assert bench.profiled_traffic("k<64>", 5000) == pytest.approx(2000)   # per hit, a larger batch
     (fake_root / "k.cu").write_text(SRC.replace("p[0] = 1", "p[1] = 1"))
     assert bench.profiled_traffic("k<64>", 1000) is None       # the code changed
 
@@ -55,4 +56,19 @@ def test_issue_roofline_arithmetic(fake_root):
     assert r["frac"] == pytest.approx(2.0 / 1216.0)
     assert r["simt_efficiency"] == pytest.approx(0.5)
     assert bench.issue_roofline("k<64>", 1000, 1.0, None, 152) is None
-    assert bench.issue_roofline("k<64>", 999, 1.0, 2000.0, 152) is None
+    # a batch twice as large in the same time issues twice the instructions
+    assert bench.issue_roofline("k<64>", 2000, 1.0, 2000.0, 152)["frac"] == pytest.approx(4.0 / 1216.0)
+
+
+def test_roofline_entry_binds_on_issue_with_counters_else_hbm(fake_root):
+    kms = [0.1, 1.0, 1.0, 0.1, 0.5]
+    r = bench.roofline_entry(64, 1000, 100.0, 6000.0, "measured", kms, 2000.0, 152, 50.0, 20.0)
+    # the search kernel's name is k_search_persistent<64>: no counters in the fake pin
+    assert r["bound"] == "hbm" and r["frac"] == pytest.approx(100.0 / 6000.0) and r["traffic"] is None
+    pin = json.loads((fake_root / "profiles" / "traffic.json").read_text())
+    pin["kernels"]["k_search_persistent<64>"] = pin["kernels"]["k<64>"]
+    (fake_root / "profiles" / "traffic.json").write_text(json.dumps(pin))
+    r = bench.roofline_entry(64, 1000, 100.0, 6000.0, "measured", kms, 2000.0, 152, 50.0, 20.0)
+    assert r["bound"] == "issue" and r["unit"] == "G warp instructions/s"
+    assert r["frac"] == pytest.approx(2.0 / 1216.0) and r["hbm_frac"] == pytest.approx(100.0 / 6000.0)
+    assert r["traffic"] == 400 and r["simt_efficiency"] == pytest.approx(0.5)

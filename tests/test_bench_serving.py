@@ -30,7 +30,10 @@ class FakeServer:
 
     def stats(self):
         return {"batches": self.batches, "mean_batch_events": self.events_batched / self.batches,
-                "peak_bytes": 3 << 30, "feed_lag_s": 2e-4, "launch_busy_s": self.busy}
+                "peak_bytes": 3 << 30, "feed_lag_s": 2e-4, "launch_busy_s": self.busy,
+                "upload_ms": 0.5 * self.batches, "kernel_ms": 2.0 * self.batches,
+                "download_ms": 0.25 * self.batches, "batch_wall_ms": 4.0 * self.batches,
+                "timed_batches": self.batches}
 
     def submit_schedule(self, ev, arrival, first_id=0):
         assert first_id == 0
@@ -59,6 +62,9 @@ def test_all_at_once_span_is_the_largest_latency():
     assert r["launcher_busy_fraction"] == pytest.approx(0.25 / span)
     assert r["generator_max_lag_ms"] == pytest.approx(0.2)
     assert r["budget_gb"] == 4.0
+    # per-batch split from this run's counter differences
+    assert r["per_batch_ms"] == pytest.approx({"upload_ms": 0.5, "kernel_ms": 2.0, "download_ms": 0.25,
+                                               "batch_wall_ms": 4.0})
 
 
 def test_open_loop_span_runs_from_first_arrival_to_last_completion():

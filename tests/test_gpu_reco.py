@@ -424,9 +424,17 @@ def test_autotune_keeps_results(sbt):
     ev = synth.make_events(2, 300, workers=1)
     h = sbt.sbt_create(MZ, sbt.default_config(**CFG))
     try:
-        chosen = sbt.sbt_autotune(h, *to_dev(ev))
-        assert chosen in (64, 128, 256)
-        assert_same(run_gpu(sbt, h, ev, True), oracle_of(ev))
+        chosen, per_sm = sbt.sbt_autotune(h, *to_dev(ev))
+        assert chosen in (64, 128, 256) and per_sm >= 1
+        assert sbt.sbt_tuned_shape(h) == (chosen, per_sm)
+        o = oracle_of(ev)
+        assert_same(run_gpu(sbt, h, ev, True), o)
+        # any launch shape gives the same tracks
+        for shape in ((64, 3), (128, 1), (256, 0)):
+            sbt.sbt_set_launch_shape(h, *shape)
+            assert_same(run_gpu(sbt, h, ev, True), o)
+        with pytest.raises(sbt.SbtError):
+            sbt.sbt_set_launch_shape(h, 96, 4)
     finally:
         h.close()
 
