@@ -153,7 +153,7 @@ __device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* par
 
 enum Misc {
     kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kNOuter = 7,
-    kNew = 8, kWork = 9, kMiscN = 32
+    kNew = 8, kWork = 9, kCMask = 10, kMiscN = 32
 };
 
 // Per-block shared memory of the search: flag bits, module offsets, counters.
@@ -242,7 +242,8 @@ struct Region {
     const uint16_t* phi;
     uint32_t* list;
     uint16_t* prev;
-    unsigned long long* claim;
+    unsigned long long* claim;  // the search's claim of sorted position p is claim[p & cmask]
+    unsigned cmask;
     unsigned long long* tracklets;
     uint32_t* tl_q;
     int lcap;
@@ -261,6 +262,7 @@ __device__ inline Region<HS> region_of(const Sorted& O, int off, const Work& W, 
     R.list = W.list + hb;
     R.prev = W.prev + hb;
     R.claim = W.claim + hb;
+    R.cmask = ~0u;
     R.tracklets = W.tracklets + hb + r;
     R.tl_q = W.tl_q + hb + r;
     R.lcap = cap + 1;
@@ -831,11 +833,11 @@ __device__ __forceinline__ void follow_and_claim(const DevConfig& C, const Smem&
         T.cand = (uint16_t)b;
         T.sc = sc;
         const unsigned long long k = claim_key(tag, sc, T.key);
-        atomicMin(&R.claim[b], k);
+        atomicMin(&R.claim[b & R.cmask], k);
         if (T.nh == 3) {
-            atomicMin(&R.claim[T.h0], k);
-            atomicMin(&R.claim[T.h1], k);
-            atomicMin(&R.claim[T.h2], k);
+            atomicMin(&R.claim[T.h0 & R.cmask], k);
+            atomicMin(&R.claim[T.h1 & R.cmask], k);
+            atomicMin(&R.claim[T.h2 & R.cmask], k);
         }
     } else {
         T.cand = kNone;
@@ -885,7 +887,7 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
             misc[kWork] = 0;
         }
         if (s + 3 <= M - 1)  // claim words of the target module start empty
-            for (int p = S.modoff[s + 3] + tid; p < S.modoff[s + 4]; p += NT) R.claim[p] = ~0ull;
+            for (int p = S.modoff[s + 3] + tid; p < S.modoff[s + 4]; p += NT) R.claim[p & R.cmask] = ~0ull;
         const int c0 = S.modoff[s + 1], c1 = S.modoff[s + 2];
         uint32_t* outer = list + (c1 - c0);
         for (int base = c0 + (tid & ~31); base < c1; base += NT) {
@@ -956,12 +958,12 @@ __device__ bool search_stage(const DevConfig& C, const Region<HS>& R, const Smem
                 if (T.cand != kNone) {
                     const unsigned long long k = claim_key(tag, T.sc, T.key);
                     // all claim words loaded at once (one round trip)
-                    const unsigned long long c0 = __ldcg(&R.claim[T.cand]);
+                    const unsigned long long c0 = __ldcg(&R.claim[T.cand & R.cmask]);
                     unsigned long long c1 = k, c2 = k, c3 = k;
                     if (T.nh == 3) {
-                        c1 = __ldcg(&R.claim[T.h0]);
-                        c2 = __ldcg(&R.claim[T.h1]);
-                        c3 = __ldcg(&R.claim[T.h2]);
+                        c1 = __ldcg(&R.claim[T.h0 & R.cmask]);
+                        c2 = __ldcg(&R.claim[T.h1 & R.cmask]);
+                        c3 = __ldcg(&R.claim[T.h2 & R.cmask]);
                     }
                     won = c0 == k && c1 == k && c2 == k && c3 == k;
                 }
@@ -1011,6 +1013,15 @@ __device__ void tracklet_filter(const DevConfig& C, const Region<HS>& R, const S
 {
     const int tid = threadIdx.x;
     const int ntl = min(S.misc[kNTl], R.lcap);
+    // the search kept its claims in a ring; the filter's claims use the whole
+    // array, the tracklets' words cleared first
+    for (int k = tid; k < ntl; k += NT) {
+        const unsigned long long v = R.tracklets[k];
+        R.claim[v & 0xFFFF] = ~0ull;
+        R.claim[(v >> 16) & 0xFFFF] = ~0ull;
+        R.claim[(v >> 32) & 0xFFFF] = ~0ull;
+    }
+    __syncthreads();
     for (int k = tid; k < ntl; k += NT) {
         unsigned long long v = R.tracklets[k];
         int h[3] = {(int)(v & 0xFFFF), (int)((v >> 16) & 0xFFFF), (int)((v >> 32) & 0xFFFF)};
@@ -1121,8 +1132,23 @@ __device__ void run_event(const DevConfig& C, const Inputs& in, const Sorted& O,
     for (int m = tid; m <= C.M; m += NT) S.modoff[m] = O.modoff[(int64_t)e * (C.M + 1) + m];
     for (int w = tid; w < (n + 31) / 32; w += NT) S.flag[w] = 0u;
     __syncthreads();
+    // Claims are live only on the modules s-1 .. s+3 of step s (a 3-hit track
+    // has its hits on s-1 or later, a new hit lies on s+3), so the search keeps
+    // them in a ring of the smallest power of two that covers every such span:
+    // live positions never share a slot, and the ring stays in cache.  Without
+    // such a power of two within the region's capacity, no ring.
+    if (tid == 0) {
+        int w = 0;
+        for (int s = 0; s + 2 <= C.M - 1; s++)
+            w = max(w, S.modoff[min(s + 4, C.M)] - S.modoff[max(s - 1, 0)]);
+        int p2 = 1;
+        while (p2 < w && p2 <= cap) p2 <<= 1;
+        S.misc[kCMask] = p2 >= w && p2 <= cap ? p2 - 1 : -1;
+    }
+    __syncthreads();
+    R.cmask = (unsigned)S.misc[kCMask];
     // claim words of the modules that are never a following target
-    for (int p = tid; p < S.modoff[min(3, C.M)]; p += NT) R.claim[p] = ~0ull;
+    for (int p = tid; p < S.modoff[min(3, C.M)]; p += NT) R.claim[p & R.cmask] = ~0ull;
     __syncthreads();
     if (!search_stage<NT, GEO>(C, R, S, n)) {
         fail_event(e, SBT_ERR_CAPACITY, G, out);
