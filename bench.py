@@ -731,7 +731,10 @@ def main():
                 serve(sbt, servers[b], ev_srv, None, b)  # warm-up: buffers and pools reach size
             return servers[b]
         try:
-            sat = serve(sbt, server(8 << 30), ev_srv, None, 8 << 30)   # all events at once
+            # all events at once, three times: the host-to-device copies share the
+            # host with other work, so the median run stands for saturation
+            sats = [serve(sbt, server(8 << 30), ev_srv, None, 8 << 30) for _ in range(3)]
+            sat = sorted(sats, key=lambda r: r["value"])[1]
             at9 = serve(sbt, server(8 << 30), ev_srv, 0.9 * sat["value"], 8 << 30)
             runs = [serve(sbt, server(b), ev_srv, f * sat["value"], b) for b in budgets for f in rates]
         finally:
@@ -741,6 +744,9 @@ def main():
                    "server": f"long-lived, {SERVE_STREAMS} stream slots, batches of at most {SERVE_BATCH} "
                              "events, warmed up by one schedule of the same events",
                    "saturation": sat, "at_0.9x": at9, "runs": runs,
+                   "saturation_runs": [{"value": r["value"], "p99_ms": r["p99_ms"],
+                                        "upload_ms_per_batch": (r["per_batch_ms"] or {}).get("upload_ms")}
+                                       for r in sats],
                    "p99_ms_at_0.9x": at9["p99_ms"]}
     h.close()
 

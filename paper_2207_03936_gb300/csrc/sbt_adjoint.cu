@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
     __syncthreads();
     double* my = acc + warp * P;
     const double s2 = (double)C.sigma * (double)C.sigma;
+    const double inv_s2 = 1.0 / s2, two_inv_s2 = 2.0 * inv_s2;  // one fp64 division per launch
     const int gw = blockIdx.x * kAdjWarps + warp;
     const int nw = gridDim.x * kAdjWarps;
     const int64_t end = n_tracks > 0 ? hit_offsets[n_tracks] : 0;
@@ -203,8 +204,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
                 const double dz = a.pz - zm;
                 const double rx = (a.px - xm) - tx * dz;
                 const double ry = (a.py - ym) - ty * dz;
-                c2 += (rx * rx + ry * ry) / s2;
-                const double gx = 2.0 * rx / s2, gy = 2.0 * ry / s2, gz = -(2.0 * rx * tx + 2.0 * ry * ty) / s2;
+                c2 += (rx * rx + ry * ry) * inv_s2;
+                const double gx = rx * two_inv_s2, gy = ry * two_inv_s2, gz = -(rx * tx + ry * ty) * two_inv_s2;
                 const double* D = mats + 36 * m;
                 double ux, uy, uz;
                 g[0] = gx;
