@@ -488,27 +488,31 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort(DevConfig C, Inputs in
     for (int m = tid; m <= C.M; m += NT)
         O.modoff[(int64_t)e * (C.M + 1) + m] = m == 0 ? 0 : (m < C.M ? cnt[(m << 6) - 1] : n);
     __syncthreads();
-    // gather of the sorted hits, two per thread per round
-    for (int p0 = tid; p0 < n; p0 += 2 * NT) {
+    // phi16 by sorted position, and the sorted position of every input hit
+    // (in the space of phi16 by input order, free now)
+    uint16_t* rank = phi;
+    for (int p = tid; p < n; p += NT) {
+        const uint32_t en = ent[p];
+        O.phi[off + p] = (uint16_t)(en >> 14);
+        rank[en & 0x3FFFu] = (uint16_t)p;
+    }
+    __syncthreads();
+    // the hits in input order (coalesced loads), each stored at its sorted
+    // position; two per thread per round
+    for (int i0 = tid; i0 < n; i0 += 2 * NT) {
         float4 c[2];
-        uint32_t en[2];
+        int q[2];
 #pragma unroll
         for (int u = 0; u < 2; u++) {
-            const int p = p0 + u * NT;
-            if (p < n) {
-                en[u] = ent[p];
-                const int i = (int)(en[u] & 0x3FFFu);
+            const int i = i0 + u * NT;
+            if (i < n) {
                 c[u] = make_float4(in.x[off + i], in.y[off + i], in.z[off + i], __int_as_float(i));
+                q[u] = rank[i];
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
-            const int p = p0 + u * NT;
-            if (p < n) {
-                O.phi[off + p] = (uint16_t)(en[u] >> 14);
-                HS::store((typename HS::T*)O.coords, (int64_t)off + p, c[u]);
-            }
-        }
+        for (int u = 0; u < 2; u++)
+            if (i0 + u * NT < n) HS::store((typename HS::T*)O.coords, (int64_t)off + q[u], c[u]);
     }
     if (tid == 0) O.status[e] = SBT_OK;
 }
