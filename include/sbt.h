@@ -253,8 +253,9 @@ sbt_status sbt_debug_phi16(const float* x, const float* y, int32_t n, uint16_t* 
  * Measurement helper: runs the batched sequence `reps` times without a graph,
  * timing each kernel with CUDA events on `stream`, and writes the mean
  * milliseconds per launch to ms[5] (host): ordering kernel, sort kernel,
- * persistent search kernel, scan, output (canonical order, hit lists and
- * fits into the CSR arrays).  Synchronous.
+ * persistent search kernel, scan, output (the output kernel's canonical
+ * order and CSR starts, then the fit kernel's hit lists and fits).
+ * Synchronous.
  */
 sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, const float* z,
                                const int32_t* module, const int32_t* event_offsets,
@@ -269,7 +270,7 @@ sbt_status sbt_profile_batched(sbt_handle* h, const float* x, const float* y, co
  * application that owns the device memory pool.  The paper has no
  * counterpart; it computes exactly what sbt_reconstruct computes.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *     workspace is a fixed array of about 46 MB inside the library's device
+ *     workspace is a fixed array of about 48 MB inside the library's device
  *     image, held by every GPU that loads the library until the process exits.
  *   - At most 524288 hits and 4096 events per call; larger batches return
  *     SBT_ERR_ARG with a message from sbt_last_error (split the batch).

@@ -116,6 +116,7 @@ size_t carve_staging(void* base, int64_t n_hits, int64_t n_events, Staging* S)
     s.tkey = c.take<int32_t>(n_hits / 3 + n_events + 1);
     s.tinfo = c.take<uint32_t>(n_hits / 3 + n_events + 1);
     s.rinfo = c.take<uint32_t>(n_hits / 3 + n_events + 1);
+    s.tfit = c.take<uint2>(n_hits / 3 + n_events + 1);
     s.ev_ntracks = c.take<int32_t>(n_events);
     s.ev_nhits = c.take<int32_t>(n_events);
     s.track_base = c.take<int32_t>(n_events);
@@ -426,7 +427,7 @@ sbt_status sbt_reconstruct(sbt_handle* h, const float* x, const float* y, const 
     if (e == cudaSuccess) e = launch_plain(h->C, in, O, W, S, *out, default_threads(h, false), s);
     if (e == cudaSuccess) e = launch_finish(h->C, in, S, *out, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "plain launch");
-    h->launches_last = n_events > 0 ? 4 : 2;
+    h->launches_last = n_events > 0 ? 5 : 2;
     return SBT_OK;
 }
 
@@ -490,7 +491,7 @@ sbt_status sbt_reconstruct_batched(sbt_handle* h, const float* x, const float* y
     }
     cudaError_t e = cudaGraphLaunch(h->exec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
-    h->launches_last = n_events > 0 ? 5 : 2;
+    h->launches_last = n_events > 0 ? 6 : 2;
     return SBT_OK;
 }
 
@@ -609,6 +610,8 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
         Sc.hit_base = S.hit_base + ev0;
         Sc.order = S.order + ev0;
         Sc.queue = S.queue + 4 * c;
+        // Sc.tfit is indexed by the chunk's own track numbers: the chunks'
+        // output and fit kernels run one after the other on one stream
     };
     for (int c = 0; c < C && e == cudaSuccess; c++) {
         const int32_t Ec = e0[c + 1] - e0[c];
@@ -695,7 +698,7 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     oh->counts[1] = (int32_t)HH;
     oh->counts[2] = cap_ok ? SBT_OK : SBT_ERR_CAPACITY;
     oh->counts[3] = (int32_t)failed;
-    h->launches_last = C * 6;
+    h->launches_last = C * 7;
     return SBT_OK;
 }
 

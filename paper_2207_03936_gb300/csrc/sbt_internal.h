@@ -83,16 +83,17 @@ struct Work {
 struct Staging {
     float4* hits;         // [n_hits]: event e from event_offsets[e], each track's hit records
                           // contiguous in traversal order, tracks in found order
-                          // (x, y, z as stored, event-local input index as int bits)
+                          // (x, y, z as stored, batch input index as int bits)
     int32_t* tkey;        // [n_hits / 3 + n_events + 1] smallest input index of each found track
     uint32_t* tinfo;      // same indexing: first staged hit | hits << 16, found order
     uint32_t* rinfo;      // same indexing: tinfo of the track of each rank (output kernel)
+    uint2* tfit;          // same size, by batch track index: first staged hit, hits (fit kernel)
     int32_t* ev_ntracks;  // [n_events]
     int32_t* ev_nhits;    // [n_events]
     int32_t* track_base;  // [n_events]
     int32_t* hit_base;    // [n_events]
     int32_t* order;       // [n_events] processing order of the persistent launch
-    int32_t* queue;       // [4]      work-queue head
+    int32_t* queue;       // [4]      work-queue head; [1]: tracks the output kernel writes
 };
 
 // Sizes of the scratch arrays for `hits` hit slots over `regions` regions.

@@ -30,7 +30,7 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Layout {
     size_t coords, phi, modoff, status;
     size_t list, prev, claim, ft, tracklets, tl_q, finals;
-    size_t hits, tkey, tinfo, rinfo, ntracks, nhits, track_base, hit_base, order, queue, total;
+    size_t hits, tkey, tinfo, rinfo, tfit, ntracks, nhits, track_base, hit_base, order, queue, total;
 };
 
 constexpr Layout make_layout()
@@ -54,6 +54,7 @@ constexpr Layout make_layout()
     L.tkey = o;       o = align256(o + 4 * (size_t)(H / 3 + E + 1));
     L.tinfo = o;      o = align256(o + 4 * (size_t)(H / 3 + E + 1));
     L.rinfo = o;      o = align256(o + 4 * (size_t)(H / 3 + E + 1));
+    L.tfit = o;       o = align256(o + 8 * (size_t)(H / 3 + E + 1));
     L.ntracks = o;    o = align256(o + 4 * (size_t)E);
     L.nhits = o;      o = align256(o + 4 * (size_t)E);
     L.track_base = o; o = align256(o + 4 * (size_t)E);
@@ -66,7 +67,7 @@ constexpr Layout make_layout()
 
 constexpr Layout kLayout = make_layout();
 
-// The workspace (about 46 MB).  In host code this name is only a host-side
+// The workspace (about 48 MB).  In host code this name is only a host-side
 // stand-in: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_workspace[kLayout.total];
 
@@ -149,6 +150,7 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
     S.tkey = (int32_t*)(base + L.tkey);
     S.tinfo = (uint32_t*)(base + L.tinfo);
     S.rinfo = (uint32_t*)(base + L.rinfo);
+    S.tfit = (uint2*)(base + L.tfit);
     S.ev_ntracks = (int32_t*)(base + L.ntracks);
     S.ev_nhits = (int32_t*)(base + L.nhits);
     S.track_base = (int32_t*)(base + L.track_base);
@@ -176,6 +178,6 @@ extern "C" sbt_status sbt_reconstruct_noalloc(sbt_handle* h, const float* x, con
         handle_set_error(h, std::string("noalloc launch: ") + cudaGetErrorString(e));
         return SBT_ERR_CUDA;
     }
-    handle_set_launches(h, n_events > 0 ? 4 : 2);
+    handle_set_launches(h, n_events > 0 ? 5 : 2);
     return SBT_OK;
 }

@@ -1093,8 +1093,8 @@ __device__ void output_stage(int e, int off, const Region<HS>& R, const Smem& S,
         for (int j = nh - 1; j >= 0; j--) {
             const int nq = R.prev[q];
             const float4 c = R.coords[q];
-            hits[u + j] = c;
             const int i = __float_as_int(c.w);
+            hits[u + j] = make_float4(c.x, c.y, c.z, __int_as_float(off + i));
             mn = i < mn ? i : mn;
             q = nq;
         }
@@ -1243,8 +1243,10 @@ __global__ void __launch_bounds__(1024) k_order(Inputs in, Staging G)
 __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks out)
 {
     __shared__ int wsum[33];
+    __shared__ int first_over;
     const int tid = threadIdx.x;
     const int E = in.n_events;
+    if (tid == 0) first_over = INT_MAX;
     const int chunk = (E + 1023) / 1024;
     const int beg = min(E, tid * chunk), end = min(E, beg + chunk);
     int t = 0, h = 0, f = 0;
@@ -1261,10 +1263,15 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
         G.track_base[e] = bt;
         G.hit_base[e] = bh;
         out.track_offsets[e] = bt;
+        // the output kernel skips the events past the capacities: a suffix
+        if ((int64_t)bt + G.ev_ntracks[e] > out.cap_tracks || (int64_t)bh + G.ev_nhits[e] > out.cap_hits)
+            atomicMin(&first_over, bt);
         bt += G.ev_ntracks[e];
         bh += G.ev_nhits[e];
     }
+    __syncthreads();
     if (tid == 0) {
+        G.queue[1] = min(first_over, T);
         out.track_offsets[E] = T;
         bool ok = T <= out.cap_tracks && H <= out.cap_hits;
         if (ok) out.hit_offsets[T] = H;
@@ -1275,29 +1282,38 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
     }
 }
 
-// Least-squares fit of a track whose first kFitCache hit records sit in
-// registers (cx, cy, cz) and whose others are read from src; sums in hit
-// order, every operation rounded as in fit_line.
-constexpr int kFitCache = 4;
+// Least-squares fit of one track from its n staged hit records (src), with
+// its hit list written on the way (th: batch input indices): sums in hit
+// order, every operation rounded as in fit_line.  The first pass loads the
+// records four at a time (independent loads in flight) and keeps the first
+// kFitCache in registers; the two centred passes re-read the others.
+constexpr int kFitCache = 4;  // the first chunk of four loads
 
-__device__ __forceinline__ void fit_cached(int n, const float* cx, const float* cy, const float* cz,
-                                           const float4* src, float sigma, float* params, float* chi2)
+__device__ __forceinline__ void fit_staged(int n, const float4* src, int32_t* th, float sigma,
+                                           float* params, float* chi2)
 {
-    const float nf = (float)n;
+    float cx[kFitCache], cy[kFitCache], cz[kFitCache];
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int i0 = 0; i0 < n; i0 += 4) {
+        float4 v[4];
 #pragma unroll
-    for (int i = 0; i < kFitCache; i++)
-        if (i < n) {
-            sx = __fadd_rn(sx, cx[i]);
-            sy = __fadd_rn(sy, cy[i]);
-            sz = __fadd_rn(sz, cz[i]);
-        }
-    for (int i = kFitCache; i < n; i++) {
-        const float4 q = src[i];
-        sx = __fadd_rn(sx, q.x);
-        sy = __fadd_rn(sy, q.y);
-        sz = __fadd_rn(sz, q.z);
+        for (int u = 0; u < 4; u++)
+            if (i0 + u < n) v[u] = src[i0 + u];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + u < n) {
+                th[i0 + u] = __float_as_int(v[u].w);
+                sx = __fadd_rn(sx, v[u].x);
+                sy = __fadd_rn(sy, v[u].y);
+                sz = __fadd_rn(sz, v[u].z);
+                if (i0 == 0) {
+                    cx[u] = v[u].x;
+                    cy[u] = v[u].y;
+                    cz[u] = v[u].z;
+                }
+            }
     }
+    const float nf = (float)n;
     const float xm = __fdiv_rn(sx, nf), ym = __fdiv_rn(sy, nf), zm = __fdiv_rn(sz, nf);
     float szz = 0.0f, szx = 0.0f, szy = 0.0f;
     auto moments = [&](float x, float y, float z) {
@@ -1309,6 +1325,7 @@ __device__ __forceinline__ void fit_cached(int n, const float* cx, const float* 
 #pragma unroll
     for (int i = 0; i < kFitCache; i++)
         if (i < n) moments(cx[i], cy[i], cz[i]);
+#pragma unroll 4
     for (int i = kFitCache; i < n; i++) {
         const float4 q = src[i];
         moments(q.x, q.y, q.z);
@@ -1325,6 +1342,7 @@ __device__ __forceinline__ void fit_cached(int n, const float* cx, const float* 
 #pragma unroll
     for (int i = 0; i < kFitCache; i++)
         if (i < n) resid(cx[i], cy[i], cz[i]);
+#pragma unroll 4
     for (int i = kFitCache; i < n; i++) {
         const float4 q = src[i];
         resid(q.x, q.y, q.z);
@@ -1336,14 +1354,12 @@ __device__ __forceinline__ void fit_cached(int n, const float* cx, const float* 
     *chi2 = __fdiv_rn(s, __fmul_rn(sigma, sigma));
 }
 
-// Output (section "Results", data consolidation), one block per event,
-// straight into the CSR arrays: canonical order of the event's tracks by
-// smallest input hit index, their hit lists (batch input indices, traversal
-// order) and the least-squares fit of every track on its staged hit records
-// (coordinates as the hit storage keeps them).  A track's rank is the number
-// of tracks with a smaller smallest index: one bit per input index marks the
-// tracks' smallest indices (shared memory), and a prefix of the words' bit
-// counts gives every rank.
+// Output (section "Results", data consolidation), one block per event: the
+// canonical order of the event's tracks by smallest input hit index and
+// their CSR starts; the hit lists and fits follow in k_fit.  A track's rank
+// is the number of tracks with a smaller smallest index: one bit per input
+// index marks the tracks' smallest indices (shared memory), and a prefix of
+// the words' bit counts gives every rank.
 constexpr int kOutputThreads = 256;
 
 __global__ void __launch_bounds__(kOutputThreads) k_output(DevConfig C, Inputs in, Staging G,
@@ -1402,30 +1418,33 @@ __global__ void __launch_bounds__(kOutputThreads) k_output(DevConfig C, Inputs i
     for (int r = beg; r < end; r++) {
         const uint32_t ri = G.rinfo[slot0 + r];
         const int nh = (int)(ri >> 16);
-        const float4* src = G.hits + off + (ri & 0xFFFFu);
         const int64_t g = (int64_t)tb + r;
-        const int64_t h0 = (int64_t)hbase + cs;
-        out.hit_offsets[g] = (int32_t)h0;
-        float cx[kFitCache], cy[kFitCache], cz[kFitCache];
-#pragma unroll
-        for (int i = 0; i < kFitCache; i++)
-            if (i < nh) {
-                const float4 q = src[i];
-                cx[i] = q.x;
-                cy[i] = q.y;
-                cz[i] = q.z;
-                out.track_hits[h0 + i] = off + __float_as_int(q.w);
-            }
-        for (int i = kFitCache; i < nh; i++) out.track_hits[h0 + i] = off + __float_as_int(src[i].w);
-        float p[4], chi2;
-        fit_cached(nh, cx, cy, cz, src, C.sigma, p, &chi2);
-        out.params[4 * g + 0] = p[0];
-        out.params[4 * g + 1] = p[1];
-        out.params[4 * g + 2] = p[2];
-        out.params[4 * g + 3] = p[3];
-        out.chi2[g] = chi2;
-        out.ndof[g] = 2 * nh - 4;
+        out.hit_offsets[g] = hbase + cs;
+        G.tfit[g] = make_uint2((uint32_t)(off + (int)(ri & 0xFFFFu)), (uint32_t)nh);
         cs += nh;
+    }
+}
+
+// Hit lists and least-squares fits of the canonical tracks, one thread per
+// track of the batch, in canonical order (a warp's hit lists and parameters
+// are contiguous in the output): the tracks of the events the output kernel
+// wrote, G.queue[1] of them.
+constexpr int kFitThreads = 256;
+
+__global__ void __launch_bounds__(kFitThreads) k_fit(DevConfig C, Staging G, sbt_tracks out)
+{
+    const int T = G.queue[1];
+    for (int g = blockIdx.x * kFitThreads + threadIdx.x; g < T; g += gridDim.x * kFitThreads) {
+        const uint2 f = G.tfit[g];
+        const int n = (int)f.y;
+        float p[4], chi2;
+        fit_staged(n, G.hits + f.x, out.track_hits + out.hit_offsets[g], C.sigma, p, &chi2);
+        out.params[4 * (int64_t)g + 0] = p[0];
+        out.params[4 * (int64_t)g + 1] = p[1];
+        out.params[4 * (int64_t)g + 2] = p[2];
+        out.params[4 * (int64_t)g + 3] = p[3];
+        out.chi2[g] = chi2;
+        out.ndof[g] = 2 * n - 4;
     }
 }
 
@@ -1602,6 +1621,15 @@ cudaError_t launch_output(const DevConfig& C, const Inputs& in, const Staging& S
     cudaError_t err = cudaFuncSetAttribute(k_output, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     if (in.n_events > 0) k_output<<<in.n_events, kOutputThreads, sm, stream>>>(C, in, S, out);
+    err = cudaGetLastError();
+    if (err != cudaSuccess || in.n_events == 0) return err;
+    // k_fit: one resident wave over the device, a grid-stride loop over the tracks
+    int dev = 0, sms = 0, per_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit, kFitThreads, 0);
+    if (err != cudaSuccess) return err;
+    k_fit<<<sms * std::max(per_sm, 1), kFitThreads, 0, stream>>>(C, S, out);
     return cudaGetLastError();
 }
 
