@@ -370,7 +370,7 @@ sbt_status sbt_create(const sbt_geometry* geometry, const sbt_config* cfg, sbt_h
         delete h;
         return SBT_ERR_CUDA;
     }
-    if (sort_smem_bytes(h->C.nmax) > (size_t)max_optin || smem_bytes(h->C.nmax, 256) > (size_t)max_optin) {
+    if (sort_smem_bytes(h->C.nmax) > (size_t)max_optin || smem_bytes(h->C.nmax, 256, h->C.M) > (size_t)max_optin) {
         g_create_error = "max_hits_per_event exceeds shared memory";
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         delete h;

@@ -100,7 +100,7 @@ struct Staging {
 inline int64_t tracklet_entries(int64_t hits, int64_t regions) { return hits + regions + 1; }
 inline int64_t final_entries(int64_t hits, int64_t regions) { return hits / 3 + regions + 1; }
 
-size_t smem_bytes(int nmax, int threads);
+size_t smem_bytes(int nmax, int threads, int M);
 size_t sort_smem_bytes(int nmax);
 
 // Launchers (sbt_reco.cu).  All asynchronous on `stream`.

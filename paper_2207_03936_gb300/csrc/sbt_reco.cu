@@ -153,12 +153,14 @@ __device__ __forceinline__ void fit_line(int n, Get get, float sigma, float* par
 
 enum Misc {
     kErr = 0, kCnt0 = 1, kCnt1 = 2, kNFin = 3, kNTl = 4, kEvent = 5, kList = 6, kNOuter = 7,
-    kNew = 8, kWork = 9, kCMask = 10, kMiscN = 32
+    kNew = 8, kWork = 9, kCMask = 10, kMiscN = 12
 };
 
-// Per-block shared memory of the search: flag bits, module offsets, counters.
-// Everything sized by the event lives in global scratch (L1-resident), so a
-// block needs about 2 KB plus n/8 bytes and many events are in flight per SM.
+// Per-block shared memory of the search: flag bits, module offsets, counters,
+// each sized to what the configuration needs.  Everything sized by the event
+// lives in global scratch (L1-resident): shared memory and L1 share one array
+// per SM, so every byte a block holds here comes out of the L1 of 32 resident
+// events (about n / 8 + 4 M bytes a block).
 struct Smem {
     uint32_t* flag;     // one bit per sorted position
     int* modoff;
@@ -172,24 +174,23 @@ struct Plan {
     size_t flag, modoff, misc, wsum, total;
 };
 
-__host__ __device__ inline Plan make_plan(int nmax, int threads)
+__host__ __device__ inline Plan make_plan(int nmax, int threads, int M)
 {
-    (void)threads;
     Plan p;
     size_t o = 0;
     p.flag = o;     o = align16(o + 4 * (((size_t)nmax + 31) / 32));
-    p.modoff = o;   o = align16(o + 4 * (kMaxModules + 1));
+    p.modoff = o;   o = align16(o + 4 * ((size_t)M + 1));
     p.misc = o;     o = align16(o + 4 * kMiscN);
-    p.wsum = o;     o = align16(o + 4 * 40);
+    p.wsum = o;     o = align16(o + 4 * ((size_t)threads / 32 + 1));
     p.total = o;
     return p;
 }
 
-size_t smem_bytes(int nmax, int threads) { return make_plan(nmax, threads).total; }
+size_t smem_bytes(int nmax, int threads, int M) { return make_plan(nmax, threads, M).total; }
 
-__device__ inline Smem carve(unsigned char* raw, int nmax, int threads)
+__device__ inline Smem carve(unsigned char* raw, int nmax, int threads, int M)
 {
-    Plan p = make_plan(nmax, threads);
+    Plan p = make_plan(nmax, threads, M);
     Smem S;
     S.flag = (uint32_t*)(raw + p.flag);
     S.modoff = (int*)(raw + p.modoff);
@@ -273,7 +274,7 @@ __device__ inline Region<HS> region_of(const Sorted& O, int off, const Work& W, 
 }
 
 // Exclusive block scan of one int per thread; returns the prefix, *total the
-// sum.  wsum needs 33 entries.
+// sum.  wsum needs NT / 32 + 1 entries.
 template <int NT>
 __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total)
 {
@@ -295,11 +296,11 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
             if (lane >= o) wi += t;
         }
         if (lane < NT / 32) wsum[lane] = wi - w;
-        if (lane == NT / 32 - 1) wsum[32] = wi;
+        if (lane == NT / 32 - 1) wsum[NT / 32] = wi;
     }
     __syncthreads();
     int res = wsum[warp] + incl - v;
-    *total = wsum[32];
+    *total = wsum[NT / 32];
     __syncthreads();
     return res;
 }
@@ -1177,7 +1178,7 @@ __global__ void __launch_bounds__(NT, kSearchThreadsPerSM / NT) k_search_plain(D
                                                       Staging G, sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, C.nmax, NT);
+    Smem S = carve(smem_raw, C.nmax, NT, C.M);
     const int e = blockIdx.x;
     const int off = in.offsets[e];
     const int n = in.offsets[e + 1] - off;
@@ -1192,7 +1193,7 @@ __global__ void __launch_bounds__(NT, kSearchThreadsPerSM / NT) k_search_persist
                                                            Staging G, sbt_tracks out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, C.nmax, NT);
+    Smem S = carve(smem_raw, C.nmax, NT, C.M);
     const int64_t hb = (int64_t)blockIdx.x * C.nmax;
     for (;;) {
         if (threadIdx.x == 0) S.misc[kEvent] = atomicAdd(&G.queue[0], 1);
@@ -1285,14 +1286,16 @@ __global__ void __launch_bounds__(1024) k_scan(Inputs in, Staging G, sbt_tracks 
 // Least-squares fit of one track from its n staged hit records (src), with
 // its hit list written on the way (th: batch input indices): sums in hit
 // order, every operation rounded as in fit_line.  The first pass loads the
-// records four at a time (independent loads in flight) and keeps the first
-// kFitCache in registers; the two centred passes re-read the others.
-constexpr int kFitCache = 4;  // the first chunk of four loads
+// records four at a time (independent loads in flight) and keeps the
+// coordinates of the first kFitStash in shared memory (stash: this thread's
+// column of a [kFitStash][kFitThreads] float3 array, conflict-free); the two
+// centred passes read them there and re-read only the others.
+constexpr int kFitThreads = 256;
+constexpr int kFitStash = 16;
 
-__device__ __forceinline__ void fit_staged(int n, const float4* src, int32_t* th, float sigma,
+__device__ __forceinline__ void fit_staged(int n, const float4* src, int32_t* th, float3* stash, float sigma,
                                            float* params, float* chi2)
 {
-    float cx[kFitCache], cy[kFitCache], cz[kFitCache];
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     for (int i0 = 0; i0 < n; i0 += 4) {
         float4 v[4];
@@ -1306,13 +1309,10 @@ __device__ __forceinline__ void fit_staged(int n, const float4* src, int32_t* th
                 sx = __fadd_rn(sx, v[u].x);
                 sy = __fadd_rn(sy, v[u].y);
                 sz = __fadd_rn(sz, v[u].z);
-                if (i0 == 0) {
-                    cx[u] = v[u].x;
-                    cy[u] = v[u].y;
-                    cz[u] = v[u].z;
-                }
+                if (i0 + u < kFitStash) stash[(i0 + u) * kFitThreads] = make_float3(v[u].x, v[u].y, v[u].z);
             }
     }
+    const int ns = min(n, kFitStash);
     const float nf = (float)n;
     const float xm = __fdiv_rn(sx, nf), ym = __fdiv_rn(sy, nf), zm = __fdiv_rn(sz, nf);
     float szz = 0.0f, szx = 0.0f, szy = 0.0f;
@@ -1322,11 +1322,12 @@ __device__ __forceinline__ void fit_staged(int n, const float4* src, int32_t* th
         szx = __fadd_rn(szx, __fmul_rn(dz, __fsub_rn(x, xm)));
         szy = __fadd_rn(szy, __fmul_rn(dz, __fsub_rn(y, ym)));
     };
-#pragma unroll
-    for (int i = 0; i < kFitCache; i++)
-        if (i < n) moments(cx[i], cy[i], cz[i]);
 #pragma unroll 4
-    for (int i = kFitCache; i < n; i++) {
+    for (int i = 0; i < ns; i++) {
+        const float3 q = stash[i * kFitThreads];
+        moments(q.x, q.y, q.z);
+    }
+    for (int i = kFitStash; i < n; i++) {
         const float4 q = src[i];
         moments(q.x, q.y, q.z);
     }
@@ -1339,11 +1340,12 @@ __device__ __forceinline__ void fit_staged(int n, const float4* src, int32_t* th
         const float ry = __fsub_rn(__fsub_rn(y, ym), __fmul_rn(ty, dz));
         s = __fadd_rn(s, __fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)));
     };
-#pragma unroll
-    for (int i = 0; i < kFitCache; i++)
-        if (i < n) resid(cx[i], cy[i], cz[i]);
 #pragma unroll 4
-    for (int i = kFitCache; i < n; i++) {
+    for (int i = 0; i < ns; i++) {
+        const float3 q = stash[i * kFitThreads];
+        resid(q.x, q.y, q.z);
+    }
+    for (int i = kFitStash; i < n; i++) {
         const float4 q = src[i];
         resid(q.x, q.y, q.z);
     }
@@ -1429,16 +1431,15 @@ __global__ void __launch_bounds__(kOutputThreads) k_output(DevConfig C, Inputs i
 // track of the batch, in canonical order (a warp's hit lists and parameters
 // are contiguous in the output): the tracks of the events the output kernel
 // wrote, G.queue[1] of them.
-constexpr int kFitThreads = 256;
-
 __global__ void __launch_bounds__(kFitThreads) k_fit(DevConfig C, Staging G, sbt_tracks out)
 {
+    __shared__ float3 stash[kFitStash * kFitThreads];
     const int T = G.queue[1];
     for (int g = blockIdx.x * kFitThreads + threadIdx.x; g < T; g += gridDim.x * kFitThreads) {
         const uint2 f = G.tfit[g];
         const int n = (int)f.y;
         float p[4], chi2;
-        fit_staged(n, G.hits + f.x, out.track_hits + out.hit_offsets[g], C.sigma, p, &chi2);
+        fit_staged(n, G.hits + f.x, out.track_hits + out.hit_offsets[g], stash + threadIdx.x, C.sigma, p, &chi2);
         out.params[4 * (int64_t)g + 0] = p[0];
         out.params[4 * (int64_t)g + 1] = p[1];
         out.params[4 * (int64_t)g + 2] = p[2];
@@ -1510,7 +1511,7 @@ template <int NT, class HS, class GEO>
 static cudaError_t plain_ntg(const DevConfig& C, const Inputs& in, const Sorted& O, const Work& W,
                              const Staging& G, const sbt_tracks& out, cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
+    size_t sm = smem_bytes(C.nmax, NT, C.M);
     cudaError_t err = cudaFuncSetAttribute(k_search_plain<NT, HS, GEO>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
@@ -1546,7 +1547,7 @@ cudaError_t launch_order(const Inputs& in, const Staging& S, cudaStream_t stream
 template <int NT, class HS, class GEO>
 static int occupancy_ntg(const DevConfig& C)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
+    size_t sm = smem_bytes(C.nmax, NT, C.M);
     if (cudaFuncSetAttribute(k_search_persistent<NT, HS, GEO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
         return 0;
@@ -1578,7 +1579,7 @@ static cudaError_t persistent_ntg(const DevConfig& C, const Inputs& in, const So
                                   const Staging& G, const sbt_tracks& out, int blocks,
                                   cudaStream_t st)
 {
-    size_t sm = smem_bytes(C.nmax, NT);
+    size_t sm = smem_bytes(C.nmax, NT, C.M);
     cudaError_t err = cudaFuncSetAttribute(k_search_persistent<NT, HS, GEO>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
