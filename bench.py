@@ -87,12 +87,14 @@ def code_digest(path):
 
 
 def profiled(kernel, hits):
-    """Counters of one launch of `kernel` (name<threads>) scaled to a batch
-    of `hits` hits from the committed ncu capture (profiles/traffic.json, one
+    """Counters of one launch of `kernel` (name<threads>, or a tuple of names
+    for a step made of several kernels: their sum) scaled to a batch of
+    `hits` hits from the committed ncu capture (profiles/traffic.json, one
     kernel per capture on a batch of a few GB): DRAM bytes read and written,
     warp instructions and thread instructions issued, per hit of the captured
-    batch times `hits`.  None when the kernel code differs from the one the
-    counters were taken on (comments and whitespace aside)."""
+    batch times `hits`.  None when a kernel has no counters or its code
+    differs from the one the counters were taken on (comments and whitespace
+    aside)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -100,13 +102,17 @@ def profiled(kernel, hits):
         d = json.load(f)
     if code_digest(os.path.join(ROOT, d["source"])) != d["source_code_sha256"]:
         return None
-    k = d["kernels"].get(kernel)
-    if k is None:
-        return None
-    f = hits / k["hits"]
-    return {"dram_read_bytes": k["dram_read_bytes"] * f, "dram_write_bytes": k["dram_write_bytes"] * f,
-            "warp_inst": k["warp_inst"] * f, "thread_inst": k["thread_inst"] * f,
-            "captured_hits": k["hits"], "captured_events": k.get("events")}
+    names = (kernel,) if isinstance(kernel, str) else tuple(kernel)
+    keys = ("dram_read_bytes", "dram_write_bytes", "warp_inst", "thread_inst")
+    r = dict.fromkeys(keys, 0.0)
+    for name in names:
+        k = d["kernels"].get(name)
+        if k is None:
+            return None
+        for key in keys:
+            r[key] += k[key] * hits / k["hits"]
+        r["captured_hits"], r["captured_events"] = k["hits"], k.get("events")
+    return r
 
 
 def profiled_traffic(kernel, hits):
@@ -131,6 +137,10 @@ def issue_roofline(kernel, hits, kernel_ms, sm_mhz, sm_count):
             "simt_efficiency": k["thread_inst"] / (32.0 * k["warp_inst"])}
 
 
+# the output step: canonical order and CSR starts, then hit lists and fits
+OUTPUT_KERNELS = ("k_output", "k_fit")
+
+
 def roofline_entry(threads, hits, hbm_gbs, peak, peak_kind, kms, sm_mhz, sm_count, sort_gbs, out_gbs):
     """The dominant kernel's roofline.  The search waits on load latency, so
     the binding roof is instruction issue: warp instructions per second of the
@@ -149,9 +159,9 @@ def roofline_entry(threads, hits, hbm_gbs, peak, peak_kind, kms, sm_mhz, sm_coun
               "sort_kernel": {"achieved_gbs": sort_gbs, "frac": sort_gbs / peak,
                               "traffic": profiled_traffic("k_sort", hits),
                               "issue": issue_roofline("k_sort", hits, kms[1], sm_mhz, sm_count)},
-              "output_kernel": {"achieved_gbs": out_gbs, "frac": out_gbs / peak,
-                                "traffic": profiled_traffic("k_output", hits),
-                                "issue": issue_roofline("k_output", hits, kms[4], sm_mhz, sm_count)}}
+              "output_kernel": {"kernels": list(OUTPUT_KERNELS), "achieved_gbs": out_gbs,
+                                "frac": out_gbs / peak, "traffic": profiled_traffic(OUTPUT_KERNELS, hits),
+                                "issue": issue_roofline(OUTPUT_KERNELS, hits, kms[4], sm_mhz, sm_count)}}
     if iss is not None:
         return {"bound": "issue", "achieved": iss["achieved_ginst_s"], "peak": iss["peak_ginst_s"],
                 "unit": "G warp instructions/s", "frac": iss["frac"],
@@ -512,8 +522,9 @@ def main():
     # smallest index and placement (8 B per track) and per-event counts out
     alg_bytes = (18 * ev.n_hits + 4 * (ev.n_events + 1) + 4 * 53 * ev.n_events
                  + 16 * H + 8 * T + 12 * ev.n_events)
-    # the output kernel reads the staged records and per-track entries and
-    # writes the CSR arrays (track hits 4 B, offsets, fits, chi2, ndof 28 B per track)
+    # the output step (output and fit kernels) reads the staged records and
+    # per-track entries and writes the CSR arrays (track hits 4 B, offsets,
+    # fits, chi2, ndof 28 B per track)
     out_bytes = 16 * H + 8 * T + 16 * ev.n_events + 4 * H + 28 * T
     out_gbs = out_bytes / (kms[4] / 1e3) / 1e9
     peak, peak_kind = peaks()

@@ -72,3 +72,16 @@ def test_roofline_entry_binds_on_issue_with_counters_else_hbm(fake_root):
     assert r["bound"] == "issue" and r["unit"] == "G warp instructions/s"
     assert r["frac"] == pytest.approx(2.0 / 1216.0) and r["hbm_frac"] == pytest.approx(100.0 / 6000.0)
     assert r["traffic"] == 400 and r["simt_efficiency"] == pytest.approx(0.5)
+
+
+def test_a_step_of_several_kernels_sums_their_counters(fake_root):
+    pin = json.loads((fake_root / "profiles" / "traffic.json").read_text())
+    pin["kernels"]["k2"] = {"dram_read_bytes": 50, "dram_write_bytes": 50, "hits": 500,
+                            "warp_inst": 1_000_000, "thread_inst": 8_000_000}
+    (fake_root / "profiles" / "traffic.json").write_text(json.dumps(pin))
+    # per hit: k<64> 0.4 B, k2 0.2 B; at 1000 hits 400 + 200
+    assert bench.profiled_traffic(("k<64>", "k2"), 1000) == pytest.approx(600)
+    r = bench.issue_roofline(("k<64>", "k2"), 1000, kernel_ms=1.0, sm_mhz=2000.0, sm_count=152)
+    assert r["warp_inst"] == pytest.approx(4_000_000)
+    assert r["simt_efficiency"] == pytest.approx((32e6 + 16e6) / (32 * 4e6))
+    assert bench.profiled_traffic(("k<64>", "k3"), 1000) is None   # one of them has no counters
