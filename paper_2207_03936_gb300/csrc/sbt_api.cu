@@ -22,12 +22,21 @@ std::string g_create_error;
 // Host pipeline: events per chunk and the most chunks per call.
 // Host pipeline: batches above kChunkEvents events are cut into chunks of
 // relative sizes kChunkWeights (small first chunk: short start-up; sizes
-// growing by at most 1.6x: the next upload, at about 0.6 of the compute time
-// per event, stays hidden; smaller last chunks: short download at the end).
+// growing by at most 1.6x; smaller last chunks: short download at the end).
+// From kLargeBatchEvents on, kChunkWeightsLarge: uploads (about 0.5 us per
+// event while downloads share the link) and reconstruction (about 0.47 us
+// per event, plus about 0.7 ms per chunk for the tail of its search and its
+// short kernels) run at nearly the same rate, so after a short ramp the
+// chunks stay level at about 11k events and only the last one is small.
 constexpr int64_t kChunkEvents = 12500;
+constexpr int64_t kLargeBatchEvents = 60000;
 constexpr int kMaxChunks = 16;
 constexpr double kChunkWeights[] = {1.0, 1.6, 2.6, 4.1, 6.6, 10.5, 16.8, 8.0, 3.0};
+constexpr double kChunkWeightsLarge[] = {1.96, 2.31, 2.71, 3.19, 3.75, 4.41, 5.19,
+                                         6.01, 6.01, 6.01, 6.01, 6.01, 2.21};
 constexpr int kWeightedChunks = sizeof(kChunkWeights) / sizeof(kChunkWeights[0]);
+constexpr int kWeightedChunksLarge = sizeof(kChunkWeightsLarge) / sizeof(kChunkWeightsLarge[0]);
+static_assert(kWeightedChunks <= kMaxChunks && kWeightedChunksLarge <= kMaxChunks, "chunk tables");
 
 // One device allocation carved into aligned sub-arrays.
 struct Arena {
@@ -514,14 +523,16 @@ sbt_status sbt_reconstruct_host(sbt_handle* h, const float* x, const float* y, c
     // chunks of whole events: inputs of chunk c+1 upload while chunk c
     // computes, results of chunk c download while chunk c+1 computes
     const int64_t H = n_hits, E = n_events;
-    const int C = E > kChunkEvents ? kWeightedChunks : 1;
+    const bool large = E >= kLargeBatchEvents;
+    const double* weights = large ? kChunkWeightsLarge : kChunkWeights;
+    const int C = E > kChunkEvents ? (large ? kWeightedChunksLarge : kWeightedChunks) : 1;
     std::vector<int32_t> e0(C + 1);
     {
         double wsum = 0.0, acc = 0.0;
-        for (int c = 0; c < C; c++) wsum += C > 1 ? kChunkWeights[c] : 1.0;
+        for (int c = 0; c < C; c++) wsum += C > 1 ? weights[c] : 1.0;
         e0[0] = 0;
         for (int c = 0; c < C; c++) {
-            acc += C > 1 ? kChunkWeights[c] : 1.0;
+            acc += C > 1 ? weights[c] : 1.0;
             e0[c + 1] = c + 1 == C ? (int32_t)E : (int32_t)((double)E * acc / wsum);
         }
     }

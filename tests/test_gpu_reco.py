@@ -354,6 +354,29 @@ def test_forming_track_overflow_fails_only_that_event(sbt):
         h.close()
 
 
+def test_host_entry_large_batch_schedule_equals_device_path(sbt):
+    """From 60000 events on, the host entry point uses its thirteen-chunk
+    schedule; 64000 small events (one vertex, Poisson(6) tracks) go through
+    it and must give the one-call device path's result."""
+    ev = synth.generate(synth.Recipe(n_events=64000, pv_mode="fixed", pv_mean=1, tracks_per_pv=6.0, seed=5),
+                        workers=1)
+    h = sbt.sbt_create(ev.module_z, sbt.default_config(**CFG))
+    try:
+        g = sbt.sbt_reconstruct_batched(h, *to_dev(ev)).compact()
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        out = sbt.sbt_reconstruct_host(h, pin(ev.x), pin(ev.y), pin(ev.z), pin(ev.module),
+                                       pin(ev.event_offsets))
+        assert h.last_launch_count() == 13 * 7
+    finally:
+        h.close()
+    assert (g["event_status"] == 0).all() and g["counts"][0] > 100000
+    c = out.compact()
+    for k in ("track_offsets", "hit_offsets", "track_hits", "ndof", "event_status"):
+        assert np.array_equal(c[k], g[k]), k
+    assert np.array_equal(c["params"].view(np.uint32), g["params"].view(np.uint32))
+    assert np.array_equal(c["chi2"].view(np.uint32), g["chi2"].view(np.uint32))
+
+
 def test_output_capacity_overflow_is_reported(sbt, handle):
     ev = synth.make_events(2, 10, workers=1)
     x, y, z, m, off = to_dev(ev)
