@@ -388,6 +388,37 @@ def test_output_capacity_overflow_is_reported(sbt, handle):
     assert c[2] == sbt.SBT_ERR_CAPACITY and c[0] == o.n_tracks and c[1] == len(o.track_hits)
 
 
+def test_output_capacity_overflow_writes_the_fitting_events_only(sbt, handle):
+    """With too small a track capacity, the events that fit (a prefix of the
+    batch) get their tracks, hit lists and fits, identical to a run with room
+    to spare, and nothing is written past them."""
+    ev = synth.make_events(2, 10, workers=1)
+    dev = to_dev(ev)
+    full = sbt.sbt_reconstruct(handle, *dev).compact()
+    per_event = np.diff(full["track_offsets"])
+    assert per_event[-1] > 0
+    cap = int(full["counts"][0]) - 1                       # the last event does not fit
+    tw = int(full["track_offsets"][-2])                    # tracks of the events before it
+    hw = int(full["hit_offsets"][tw])
+    out = sbt.TrackOutput.allocate(ev.n_events, ev.n_hits, cap_tracks=cap)
+    for a in (out.hit_offsets, out.track_hits, out.ndof):
+        a.fill_(-7)
+    for a in (out.params, out.chi2):
+        a.fill_(-7.0)
+    sbt.sbt_reconstruct(handle, *dev, out=out)
+    torch.cuda.synchronize()
+    c = out.counts.cpu().numpy()
+    assert c[2] == sbt.SBT_ERR_CAPACITY and c[0] == full["counts"][0]
+    ho, th = out.hit_offsets.cpu().numpy(), out.track_hits.cpu().numpy()
+    par, chi, nd = out.params.cpu().numpy(), out.chi2.cpu().numpy(), out.ndof.cpu().numpy()
+    assert np.array_equal(ho[:tw], full["hit_offsets"][:tw]) and (ho[tw:] == -7).all()
+    assert np.array_equal(th[:hw], full["track_hits"][:hw]) and (th[hw:] == -7).all()
+    assert np.array_equal(par[:4 * tw].view(np.uint32), full["params"][:tw].reshape(-1).view(np.uint32))
+    assert (par[4 * tw:] == -7.0).all()
+    assert np.array_equal(chi[:tw].view(np.uint32), full["chi2"][:tw].view(np.uint32)) and (chi[tw:] == -7.0).all()
+    assert np.array_equal(nd[:tw], full["ndof"][:tw]) and (nd[tw:] == -7).all()
+
+
 def test_repeat_runs_are_identical(sbt, handle):
     ev = synth.make_events(2, 200, workers=1)
     a = run_gpu(sbt, handle, ev, True)
