@@ -6,8 +6,12 @@
 //     h' = Rz(g) Ry(b) Rx(a) (h - c_m) + c_m + (dx, dy, dz),  c_m = (0, 0, z_m).
 // At the least-squares optimum the derivative with respect to a hit is the
 // partial derivative at fixed line parameters (the parameters are stationary),
-//     d chi2 / d h' = 2 / sigma^2 (rx, ry, -(rx tx + ry ty)),
-// chained through d h' / d(align_m).
+//     d chi2 / d h' = 2 / sigma^2 (rx, ry, -(rx tx + ry ty)) = g,
+// chained through d h' / d(align_m): g itself for the translations, and
+// g . (dR_m/da v) for a rotation angle a, v = h - c_m.  Summed over the hits
+// of module m that is sum_ij (dR_m/da)_ij sum_h g_i v_j, so the kernel
+// accumulates per module g and the outer product g v^T (9 products a hit)
+// and the derivative matrices are applied once per module at the end.
 //
 // Layout: one warp per track, lanes over its hits in rounds of 32.  A track
 // may have any number of hits and several hits on one module; a track
@@ -103,6 +107,12 @@ __device__ __forceinline__ AHit aligned_hit(const DevConfig& C, const Inputs& in
     return a;
 }
 
+// Per-block accumulator entries: per module g (3) and g v^T (9), then chi2
+// and the skipped-track count.
+constexpr int kAdjPerModule = 12;
+
+__host__ __device__ inline int adjoint_entries(int M) { return kAdjPerModule * M + 2; }
+
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
                                                           const int32_t* hit_offsets,
                                                           const int32_t* track_hits,
@@ -111,8 +121,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = C.M;
-    const int P = 6 * M + 2;  // gradient entries, chi2, skipped tracks
-    double* mats = (double*)smem_raw;               // [M][36]
+    const int P = adjoint_entries(M);
+    double* mats = (double*)smem_raw;               // [M][36]: R and its derivatives (R used here)
     double* acc = mats + 36 * M;                    // [warps][P]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int m = tid; m < M; m += kAdjThreads) module_matrices(align + 6 * m, mats + 36 * m);
@@ -129,7 +139,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
         const int n = hit_offsets[t + 1] - h0;
         // every lane reads the same offsets, so these branches are uniform
         if (n < 2 || h0 < 0 || (int64_t)h0 + n > end) {
-            if (lane == 0) my[6 * M + 1] += 1.0;
+            if (lane == 0) my[P - 1] += 1.0;
             continue;
         }
         // pass 1: validity, sums; hits 0..63 kept in registers (two per lane)
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
             mhi = max(mhi, __shfl_xor_sync(0xFFFFFFFFu, mhi, o));
         }
         if (bad || mlo == mhi) {
-            if (lane == 0) my[6 * M + 1] += 1.0;
+            if (lane == 0) my[P - 1] += 1.0;
             continue;
         }
         auto hit_at = [&](int base, int j) -> AHit {
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
         for (int base = 0; base < n; base += 32) {
             const int j = base + lane;
             const bool act = j < n;
-            double g[6] = {0, 0, 0, 0, 0, 0};
+            double g[kAdjPerModule];
             int m = -1 - lane;  // distinct for inactive lanes
             if (act) {
                 const AHit a = hit_at(base, j);
@@ -205,31 +215,27 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
                 const double rx = (a.px - xm) - tx * dz;
                 const double ry = (a.py - ym) - ty * dz;
                 c2 += (rx * rx + ry * ry) * inv_s2;
-                const double gx = rx * two_inv_s2, gy = ry * two_inv_s2, gz = -(rx * tx + ry * ty) * two_inv_s2;
-                const double* D = mats + 36 * m;
-                double ux, uy, uz;
-                g[0] = gx;
-                g[1] = gy;
-                g[2] = gz;
-                matvec(D + 9, a.vx, a.vy, a.vz, ux, uy, uz);
-                g[3] = gx * ux + gy * uy + gz * uz;
-                matvec(D + 18, a.vx, a.vy, a.vz, ux, uy, uz);
-                g[4] = gx * ux + gy * uy + gz * uz;
-                matvec(D + 27, a.vx, a.vy, a.vz, ux, uy, uz);
-                g[5] = gx * ux + gy * uy + gz * uz;
+                g[0] = rx * two_inv_s2;
+                g[1] = ry * two_inv_s2;
+                g[2] = -(rx * tx + ry * ty) * two_inv_s2;
+                const double v[3] = {a.vx, a.vy, a.vz};
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) g[3 + 3 * i + k] = g[i] * v[k];
             }
             if (want_grad) {
                 const unsigned same = __match_any_sync(0xFFFFFFFFu, m);
                 if (!__any_sync(0xFFFFFFFFu, __popc(same) > 1)) {
                     if (act) {
 #pragma unroll
-                        for (int k = 0; k < 6; k++) my[6 * m + k] += g[k];
+                        for (int k = 0; k < kAdjPerModule; k++) my[kAdjPerModule * m + k] += g[k];
                     }
                 } else {
                     for (int l = 0; l < 32; l++) {
                         if (lane == l && act) {
 #pragma unroll
-                            for (int k = 0; k < 6; k++) my[6 * m + k] += g[k];
+                            for (int k = 0; k < kAdjPerModule; k++) my[kAdjPerModule * m + k] += g[k];
                         }
                         __syncwarp();
                     }
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
             }
         }
         c2 = warp_sum(c2);
-        if (lane == 0) my[6 * M] += c2;
+        if (lane == 0) my[P - 2] += c2;
         __syncwarp();
     }
     __syncthreads();
@@ -249,24 +255,46 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevConfig C, Inputs in,
     }
 }
 
-__global__ void k_adjoint_reduce(int M, int blocks, const double* partial, double* chi2_sum,
-                                 double* grad, int32_t* skipped)
+// Fixed-order sum of the blocks' entries, then per module: the translation
+// gradient is the summed g, each rotation gradient sum_ij (dR/d angle)_ij
+// (sum g v^T)_ij.  One block of kAdjReduceThreads >= 12 M + 2 threads.
+constexpr int kAdjReduceThreads = 1024;
+static_assert(kAdjReduceThreads >= kAdjPerModule * kMaxModules + 2, "one thread per accumulator entry");
+
+__global__ void __launch_bounds__(kAdjReduceThreads) k_adjoint_reduce(int M, int blocks, const double* partial,
+                                                                      const double* align, double* chi2_sum,
+                                                                      double* grad, int32_t* skipped)
 {
-    const int P = 6 * M + 2;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
-        double s = 0;
-        for (int b = 0; b < blocks; b++) s += partial[(int64_t)b * P + k];
-        if (k < 6 * M) {
-            if (grad) grad[k] = s;
-        } else if (k == 6 * M) {
-            *chi2_sum = s;
-        } else if (skipped) {
-            *skipped = (int32_t)s;
+    __shared__ double s[kAdjPerModule * kMaxModules + 2];
+    const int P = adjoint_entries(M);
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        double v = 0;
+        for (int b = 0; b < blocks; b++) v += partial[(int64_t)b * P + k];
+        s[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < M && grad) {
+        const int m = threadIdx.x;
+        double D[36];
+        module_matrices(align + 6 * m, D);
+        const double* a = s + kAdjPerModule * m;
+        grad[6 * m + 0] = a[0];
+        grad[6 * m + 1] = a[1];
+        grad[6 * m + 2] = a[2];
+        for (int r = 0; r < 3; r++) {
+            const double* dR = D + 9 * (r + 1);
+            double v = 0;
+            for (int ij = 0; ij < 9; ij++) v += dR[ij] * a[3 + ij];
+            grad[6 * m + 3 + r] = v;
         }
+    }
+    if (threadIdx.x == 0) {
+        *chi2_sum = s[P - 2];
+        if (skipped) *skipped = (int32_t)s[P - 1];
     }
 }
 
-size_t adjoint_partial_entries(int M, int blocks) { return (size_t)blocks * (6 * (size_t)M + 2); }
+size_t adjoint_partial_entries(int M, int blocks) { return (size_t)blocks * (size_t)adjoint_entries(M); }
 
 cudaError_t launch_adjoint(const DevConfig& C, const Inputs& in, const int32_t* hit_offsets,
                            const int32_t* track_hits, int32_t n_tracks, const double* align,
@@ -274,13 +302,13 @@ cudaError_t launch_adjoint(const DevConfig& C, const Inputs& in, const int32_t* 
                            cudaStream_t stream)
 {
     const int M = C.M;
-    size_t sm = sizeof(double) * (36 * (size_t)M + (size_t)kAdjWarps * (6 * M + 2));
+    size_t sm = sizeof(double) * (36 * (size_t)M + (size_t)kAdjWarps * adjoint_entries(M));
     cudaError_t err = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sm);
     if (err != cudaSuccess) return err;
     k_adjoint<<<W.blocks, kAdjThreads, sm, stream>>>(C, in, hit_offsets, track_hits, n_tracks,
                                                       align, W.partial, grad != nullptr);
-    k_adjoint_reduce<<<2, 256, 0, stream>>>(M, W.blocks, W.partial, chi2_sum, grad, skipped);
+    k_adjoint_reduce<<<1, kAdjReduceThreads, 0, stream>>>(M, W.blocks, W.partial, align, chi2_sum, grad, skipped);
     return cudaGetLastError();
 }
 
