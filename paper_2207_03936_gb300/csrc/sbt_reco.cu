@@ -597,9 +597,11 @@ __device__ __forceinline__ void scan_from(const Smem& S, const Region<HS>& R, in
         int e = lo_idx + k;
         if (e >= nb) e -= nb;
         const int b = b0 + e;
-        if (windowed && (((uint32_t)R.phi[b] - lo) & 0xFFFFu) > width) break;
-        if (flagged(S, b)) continue;
+        // both loads issued together (b is inside the module either way)
+        const uint32_t ph = R.phi[b];
         const float4 c = R.coords[b];
+        if (windowed && ((ph - lo) & 0xFFFFu) > width) break;
+        if (flagged(S, b)) continue;
         if (!G::on(plane, c.x)) continue;
         const float sc = scatter_of(c, xp, yp);
         if (sc < cut && better(sc, b)) take(sc, b);
